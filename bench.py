@@ -1,0 +1,349 @@
+"""Benchmark of the coupled phi-mu LBM step on one GB300 (or N independent replicas).
+
+Workload: 256^3 synthetic porous medium (Gaussian random field, porosity 0.35,
+W = 2, D_l = 0.1, D_s = 0 with anti-trapping, counter term on), D3Q19, FP32
+storage and arithmetic.  One "step" is one coupled time step n -> n+1 (the phi
+kernel and the composition kernel).  The state (2.6 GB) is far larger than L2.
+
+Prints ONE JSON line on rank 0.  `--impl reference` times the FP64 CPU oracle
+on the host cores instead (a deliberately slow baseline, not the target).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "coupled phi-mu LBM MLUPS on 1 GB300, % of HBM roofline; FP32/adjoint vs FP64 fwd"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=256, help="side of the cubic domain")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16dev", "bf16dev"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=20, help="steps of the FP64 comparison run")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2111_05960_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
+    current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d[workload][kernel]
+        if e.get("source_hash") != kernel_source_hash():
+            return None
+        return float(e["bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms in the background."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [l.strip().split(",") for l in self.file.read().splitlines() if l.strip()]
+        self.file.close()
+        os.unlink(self.file.name)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+                for n, v in zip(names, r[4:8]):
+                    if v.strip().lower() == "active":
+                        reasons.add(n)
+            except Exception:
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload(n):
+    from paper_2111_05960_gb300 import workloads as WL
+    return WL.porous_3d(n=n)
+
+
+def algorithmic_bytes(q: int, real: int, store: int):
+    """Bytes per node of each kernel: populations read once and written once, phi^n
+    read and phi^{n+1} written by the phi kernel (mu is recomputed from c and phi)."""
+    phi_kernel = 2 * q * store + 2 * real
+    c_kernel = 2 * q * store
+    return phi_kernel, c_kernel
+
+
+def cpu_baseline(model, phi0, c0, budget_s=12.0):
+    """The FP64 oracle, as it stands, on a z-slab of the same medium (periodic)."""
+    import oracle as O
+    names = O.OracleParams.__dataclass_fields__
+    nz = 16
+    sub_phi = np.ascontiguousarray(phi0[:nz])
+    sub_c = np.ascontiguousarray(c0[:nz])
+    p = O.OracleParams(**{k: getattr(model, k) for k in names})
+    p.nz = nz
+    threads = O.Oracle.threads()
+    o = O.Oracle(p, sub_phi, sub_c)
+    t = time.perf_counter()
+    o.step(1)
+    one = time.perf_counter() - t
+    steps = max(1, int(budget_s / max(one, 1e-3)))
+    t = time.perf_counter()
+    o.step(steps)
+    el = time.perf_counter() - t
+    nodes = p.nx * p.ny * nz
+    return {"value": nodes * steps / el / 1e6, "unit": "MLUPS", "cores": threads, "kind": "oracle",
+            "sample": "%dx%dx%d z-slab of the 256^3 medium, %d FP64 steps, %.1f s" % (p.nx, p.ny, nz, steps, el)}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    model, phi0, c0 = make_workload(args.n)
+    import oracle as O
+    O.build()
+    names = O.OracleParams.__dataclass_fields__
+    nz = 16
+    p = O.OracleParams(**{k: getattr(model, k) for k in names})
+    p.nz = nz
+    o = O.Oracle(p, np.ascontiguousarray(phi0[:nz]), np.ascontiguousarray(c0[:nz]))
+    o.step(max(args.warmup, 1) if args.warmup > 0 else 0)
+    t = time.perf_counter()
+    o.step(args.steps)
+    el = time.perf_counter() - t
+    nodes = p.nx * p.ny * nz
+    mlups = nodes * args.steps / el / 1e6
+    out = {"impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps * (args.n / nz),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": "porous_3d_256_d3q19", "sample": "%dx%dx%d z-slab" % (p.nx, p.ny, nz),
+                      "parallelism": "host threads"},
+           "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": O.Oracle.threads(), "kind": "oracle",
+                            "sample": "%dx%dx%d z-slab of the 256^3 medium, %d FP64 steps" % (p.nx, p.ny, nz, args.steps)},
+           "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2111_05960_gb300 import build as B
+    from paper_2111_05960_gb300 import lbpf as L
+    B.build()
+    L.load()
+
+    model, phi0, c0 = make_workload(args.n)
+    N = model.nodes
+    stream = torch.cuda.Stream()
+    prec = args.precision
+    sim = L.Simulation(model, phi0, c0, precision=prec, stream=stream.cuda_stream, lattice=L.LBPF_D3Q19)
+    q = 19
+    real = 8 if prec == "fp64" else 4
+    store = {"fp64": 8, "fp32": 4, "fp16dev": 2, "bf16dev": 2}[prec]
+
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
+                          if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else local)
+    barrier()
+    clocks.start()
+    time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    k_phi_ms, k_c_ms = sim.step_timed(args.steps)
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    m_c, m_phi = sim.mass()
+    sim.close()
+
+    ms_per_step = ms / args.steps
+    mlups = world * N * args.steps / (ms * 1e-3) / 1e6
+    hbm, hbm_src = peaks()
+    b_phi, b_c = algorithmic_bytes(q, real, store)
+    avg_phi = k_phi_ms / args.steps
+    avg_c = k_c_ms / args.steps
+    dom = ("k_phi_step", avg_phi, b_phi) if avg_phi >= avg_c else ("k_c_step", avg_c, b_c)
+    achieved = dom[2] * N / (dom[1] * 1e-3) / 1e9
+    step_bytes = (b_phi + b_c) * N
+    wl = "porous_3d_%d_d3q19_%s" % (args.n, prec)
+    roof = {"bound": "hbm", "kernel": dom[0], "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "peak_source": hbm_src + " (MEASURED_PEAKS.json hbm_gbs)" if hbm_src == "measured" else "fallback",
+            "traffic": ncu_traffic(dom[0], wl),
+            "bytes_per_node": dom[2],
+            "step": {"achieved": step_bytes / (ms_per_step * 1e-3) / 1e9,
+                     "frac": step_bytes / (ms_per_step * 1e-3) / 1e9 / hbm, "bytes_per_node": b_phi + b_c},
+            "kernel_ms": {"k_phi_step": avg_phi, "k_c_step": avg_c}}
+
+    extra = {}
+    # FP64 forward on the same GPU, for the FP32/FP64 ratio the metric asks for
+    if prec == "fp32" and args.fp64_steps > 0:
+        sim64 = L.Simulation(model, phi0, c0, precision="fp64", stream=stream.cuda_stream, lattice=L.LBPF_D3Q19)
+        sim64.step(2)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sim64.step(args.fp64_steps)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms64 = a.elapsed_time(b) / args.fp64_steps
+        sim64.close()
+        extra["fp64_forward"] = {"ms_per_step": ms64, "mlups": N / (ms64 * 1e-3) / 1e6,
+                                 "fp32_speedup": ms64 / ms_per_step}
+
+    e2e = None
+    if not args.no_e2e:
+        # end to end through the public API with host buffers: create from pinned host
+        # fields (H2D inside), K steps each followed by the FP64 mass read (D2H), and the
+        # final fields read back to pinned host memory
+        hphi = torch.from_numpy(np.ascontiguousarray(phi0)).pin_memory().numpy()
+        hc = torch.from_numpy(np.ascontiguousarray(c0)).pin_memory().numpy()
+        out_phi = torch.empty(phi0.shape, dtype=torch.float64).pin_memory().numpy()
+        out_c = torch.empty(phi0.shape, dtype=torch.float64).pin_memory().numpy()
+        barrier()
+        t0 = time.perf_counter()
+        s2 = L.Simulation(model, hphi, hc, precision=prec, stream=stream.cuda_stream, lattice=L.LBPF_D3Q19)
+        for _ in range(args.steps):
+            s2.step(1)
+            s2.mass()
+        L.lbpf_get_fields(s2.ctx, out_phi, out_c, None, 0)
+        barrier()
+        el = time.perf_counter() - t0
+        s2.close()
+        if world > 1:
+            t = torch.tensor([el], device="cuda", dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": world * N * args.steps / el / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": 2 * N * 8 / args.steps,
+               "d2h_bytes_per_step": (2 * N * 8) / args.steps + 16,
+               "includes": "create from host fields, K x (step + FP64 mass read), final phi and c read"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            cpu = cpu_baseline(model, phi0, c0)
+        except Exception as ex:  # the baseline must not sink the GPU line
+            cpu = {"value": None, "error": str(ex)}
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None,
+               "dtype": {"fp32": "f32", "fp64": "f64", "fp16dev": "f32 (f16 deviation storage)",
+                         "bf16dev": "f32 (bf16 deviation storage)"}[prec],
+               "data": "synthetic",
+               "config": {"workload": wl, "nodes": N, "lattice": "D3Q19", "porosity": 0.35, "W": 2.0,
+                          "D_l": 0.1, "D_s": 0.0, "counter_term": 1, "anti_trapping": 1,
+                          "parallelism": "replicas" if world > 1 else "single GPU",
+                          "l2": "state %.1f GB per buffer set, larger than L2 (no flush needed)"
+                                % (N * (2 * q * store + 2 * real) / 1e9)},
+               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+               "gpu_launches": 2 * args.steps, "clocks": clk,
+               "mass": {"total_c": m_c, "total_phi": m_phi}}
+        out.update(extra)
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,167 @@
+/*
+ * lbpf.h — C ABI of libgb_lbpf: the coupled phi-mu lattice Boltzmann time step
+ * of the grand-potential phase-field model of dissolution and precipitation
+ * (Boutin, Verdier & Cartalade, arXiv 2111.05960), on one GB300 GPU (sm_103a).
+ *
+ * What one time step computes (Sec. 3, in this order, all in lattice units):
+ *   - closure mu = mu_eq + c - c^co(phi), c^co = c_l^co phi + c_s^co (1 - phi)
+ *     (Eq. PotChim_Equilibirum, Eq. Coexistence_Interpol, h(phi) = phi);
+ *   - grad(phi) by directional derivatives (Eq. DerivDirec_Grad, Eq. Grad) and
+ *     the unit normal n = grad / sqrt(|grad|^2 + eps_n^2) (Eq. NormalVector);
+ *   - the phi source G_k (Eq. TermG) with S_phi of Eq. SourceTerm_Coexistence and
+ *     either the double-well term (Eq. SourceG_dw) or the counter term that
+ *     cancels curvature-driven motion (Eq. SourceG_CT);
+ *   - BGK collision and streaming of the phi populations (Eq. LBE_PhaseField_Eq,
+ *     g^eq = w_k phi, Eq. Geq_Allen-Cahn_Eq-1), new phi (Eq. Moment_Phi);
+ *   - dphi/dt by explicit Euler, anti-trapping current
+ *     j_at = a W (c_s^co - c_l^co) dphi/dt n (Eq. Anti-trapping_Equilibrium);
+ *   - the composition source H_k = gamma w_k e_k.(mu D' grad phi + j_at)
+ *     (Eq. SourceTerm_LBE_h), equilibrium h^eq (Eq. Heq_Composition), BGK
+ *     collision and streaming (Eq. LBE_Composition), c = sum_k h_k
+ *     (Eq. Moment0_LBM_Concent).
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns an lbpf_status and never throws across the ABI.
+ *   - Fields crossing the ABI are FP64, row-major [nz][ny][nx] (x fastest),
+ *     whatever the internal precision.  ptr_is_device = 0: host memory (any
+ *     alignment; pinned memory makes the copies faster); 1: device memory of
+ *     the context's GPU, 8-byte aligned.
+ *   - The caller owns every array it passes; lbpf_create copies them.  The
+ *     context owns its populations, fields and scratch; lbpf_destroy frees them.
+ *   - Work is queued on the CUDA stream given at creation (NULL = legacy default
+ *     stream).  lbpf_step returns once the kernels are queued; lbpf_mass,
+ *     lbpf_get_fields and lbpf_get_populations synchronise that stream.
+ *   - One context must not be used by two threads at once.
+ *   - After LBPF_EUNSTABLE or LBPF_ETIMEOUT the context is poisoned: every later
+ *     call except lbpf_last_error and lbpf_destroy returns LBPF_ESTATE.
+ */
+#ifndef LBPF_H
+#define LBPF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBPF_OK = 0,
+    LBPF_EINVAL = 1,      /* bad argument or parameter; nothing changed */
+    LBPF_ENOMEM = 2,      /* device allocation failed; nothing leaked */
+    LBPF_ECUDA = 3,       /* a CUDA call failed; message in lbpf_last_error */
+    LBPF_EUNSTABLE = 4,   /* non-finite field or phi far outside [0, 1] */
+    LBPF_ETIMEOUT = 5,    /* a bounded device wait ran out */
+    LBPF_ESTATE = 6,      /* context poisoned by an earlier error */
+    LBPF_EUNSUPPORTED = 7 /* option combination not built */
+} lbpf_status;
+
+typedef enum { LBPF_D2Q9 = 0, LBPF_D3Q19 = 1 } lbpf_lattice;
+
+/* Storage and arithmetic of the populations and fields.  FP64: all FP64.
+ * FP32: FP32 storage and arithmetic.  The *DEV modes store each population as a
+ * 16-bit deviation from its equilibrium (g^eq = w_k phi, h^eq of
+ * Eq. Heq_Composition) and compute in FP32.  Mass sums are FP64 in every mode. */
+typedef enum {
+    LBPF_FP64 = 0,
+    LBPF_FP32 = 1,
+    LBPF_FP32_BF16DEV = 2,
+    LBPF_FP32_FP16DEV = 3
+} lbpf_precision;
+
+typedef enum { LBPF_PERIODIC = 0, LBPF_BOUNCEBACK = 1 } lbpf_bc;
+
+/* Model parameters.  With dx = dt = 1 everything is in lattice units; otherwise
+ * W is a length and D_l, D_s are diffusivities in the same physical units, and
+ * the library converts them (W/dx, D dt/dx^2).  The relaxation times are the
+ * dimensionless tau-bar of Sec. 3.1:
+ *   M_phi = tau_g dx^2 / (3 dt)           (Sec. 3.2)
+ *   gamma = 3 dt / (tau_h dx^2)            (Sec. 3.3, Tab. 4)            */
+typedef struct {
+    int32_t nx, ny, nz;          /* nodes per axis; nz = 1 selects 2-D */
+    int32_t lattice;             /* lbpf_lattice: D2Q9 needs nz == 1, D3Q19 nz >= 1 */
+    int32_t bc[3];               /* lbpf_bc per axis (x, y, z); walls are half-way
+                                    bounce-back with mirror ghosts for grad(phi) */
+    int32_t precision;           /* lbpf_precision */
+    double dx, dt;               /* 1, 1 for lattice units */
+    double tau_g, tau_h;         /* > 0 */
+    double W;                    /* interface width, > 0 */
+    double lambda;               /* coupling constant of Eq. SourceG_ST */
+    double D_l, D_s;             /* diffusivities of liquid and solid, >= 0 */
+    double c_s_co, c_l_co;       /* coexistence compositions */
+    double mu_eq;                /* equilibrium chemical potential */
+    int32_t counter_term;        /* 1: counter term G^ct; 0: double-well G^dw */
+    int32_t anti_trapping;       /* 1: j_at included in H_k */
+    double a_at;                 /* a of j_at; < 0 selects (1 - D_s/D_l)/4 */
+    double eps_n;                /* regularisation of |grad phi| in n; default 1e-12 */
+    int32_t mass_every;          /* reserved: steps between mass corrections, 0 = off */
+    int32_t reserved;            /* set to 0 */
+} lbpf_params;
+
+typedef struct lbpf_ctx lbpf_ctx;
+
+/* Fill *p with defaults: 2-D D2Q9 64x64 periodic, FP64, dx = dt = 1,
+ * tau_g = tau_h = 0.36, W = 3, lambda = 0, D_l = D_s = 0.1, c_s^co = 1,
+ * c_l^co = 0.5, mu_eq = 0.4, counter term on, anti-trapping off, a = -1 (auto),
+ * eps_n = 1e-12.  Returns LBPF_EINVAL if p is NULL. */
+lbpf_status lbpf_default_params(lbpf_params *p);
+
+/* Create a context on the current CUDA device: validate p, allocate the
+ * populations (two ping-pong sets of g and h, SoA [k][z][y][x]) and the fields
+ * phi^n, phi^{n+1}, c^n, c^{n+1}, copy phi0 and c0 (FP64, [nz][ny][nx]) and set
+ * the populations to g_k = w_k phi0 - G_k/2 and h_k = h^eq_k - H_k/2 (the
+ * variable change of Sec. 3.1 at equilibrium, H at dphi/dt = 0).
+ * cuda_stream: a cudaStream_t (NULL = default stream).  On success *out owns
+ * everything; on failure *out is NULL and nothing is leaked.
+ * Errors: EINVAL (NULL pointers, sizes < 1, nz != 1 for D2Q9, a bounce-back
+ * axis with fewer than 2 nodes, tau <= 0, W <= 0, D < 0, unknown enum),
+ * ENOMEM, ECUDA, EUNSUPPORTED. */
+lbpf_status lbpf_create(const lbpf_params *p, const double *phi0, const double *c0,
+                        int32_t ptr_is_device, void *cuda_stream, lbpf_ctx **out);
+
+/* Queue nsteps coupled time steps (n -> n + nsteps) on the context's stream.
+ * nsteps >= 0.  Errors: EINVAL, ECUDA (launch failure), ESTATE. */
+lbpf_status lbpf_step(lbpf_ctx *ctx, int64_t nsteps);
+
+/* Total solute sum_x c and phase sum_x phi, accumulated in FP64 on the GPU
+ * (deterministic two-pass block reduction), copied to the host pointers
+ * (either may be NULL).  Synchronises the stream.  Returns LBPF_EUNSTABLE and
+ * poisons the context if a field value is non-finite or phi leaves
+ * [-0.5, 1.5]. */
+lbpf_status lbpf_mass(lbpf_ctx *ctx, double *total_c, double *total_phi);
+
+/* Copy phi, c and mu = mu_eq + c - c^co(phi) at the current step into FP64
+ * arrays [nz][ny][nx] (any of them may be NULL).  Synchronises the stream. */
+lbpf_status lbpf_get_fields(lbpf_ctx *ctx, double *phi, double *c, double *mu,
+                            int32_t ptr_is_device);
+
+/* Copy the populations g and h (post-streaming, before the next collision),
+ * FP64 [q][nz][ny][nx], q = 9 (D2Q9) or 19 (D3Q19).  For the deviation-storage
+ * modes the stored deviations are expanded back to full populations.
+ * Either pointer may be NULL.  Synchronises the stream. */
+lbpf_status lbpf_get_populations(lbpf_ctx *ctx, double *g, double *h, int32_t ptr_is_device);
+
+/* Time the kernels of nsteps steps with CUDA events recorded on the context's
+ * stream around each launch.  kernel_ms[0] accumulates the phi kernel,
+ * kernel_ms[1] the composition kernel, in milliseconds.  Synchronises. */
+lbpf_status lbpf_step_timed(lbpf_ctx *ctx, int64_t nsteps, double *kernel_ms);
+
+/* Lattice table of the population ordering used by lbpf_get_populations:
+ * *q = 9 or 19; e (optional, int32 [q][3]) the link vectors; w (optional,
+ * [q]) the weights.  D2Q9 follows Sec. 3.1 (e0 = 0, e1..e4 axis links
+ * (1,0),(0,1),(-1,0),(0,-1), e5..e8 diagonals (1,1),(-1,1),(-1,-1),(1,-1)).
+ * Needs no GPU.  Errors: EINVAL for an unknown lattice or q == NULL. */
+lbpf_status lbpf_lattice_info(int32_t lattice, int32_t *q, int32_t *e, double *w);
+
+/* Number of coupled steps taken since creation. */
+lbpf_status lbpf_get_step(const lbpf_ctx *ctx, int64_t *step);
+
+/* Free everything the context owns.  NULL-safe; returns LBPF_OK. */
+lbpf_status lbpf_destroy(lbpf_ctx *ctx);
+
+/* Last error message of ctx, or of the calling thread when ctx is NULL. */
+const char *lbpf_last_error(const lbpf_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBPF_H */

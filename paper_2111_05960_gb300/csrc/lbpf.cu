@@ -1,0 +1,511 @@
+// libgb_lbpf: runtime and C ABI of the coupled phi-mu LBM step (see lbpf.h).
+//
+// The context owns two ping-pong sets of populations (g, h; SoA [k][z][y][x])
+// and two of the fields phi, c.  A time step is the phi kernel followed by the
+// composition kernel on the context's stream; the buffer parity flips after
+// each step.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbpf.h"
+#include "step_kernels.cuh"
+
+using namespace lbpf;
+
+namespace {
+
+thread_local std::string g_thread_error;
+
+struct Dispatch;
+
+}  // namespace
+
+struct lbpf_ctx {
+    lbpf_params p;
+    StepParams sp;
+    int q = 0;
+    size_t real_size = 0, store_size = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    void* g[2] = {nullptr, nullptr};
+    void* h[2] = {nullptr, nullptr};
+    void* phi[2] = {nullptr, nullptr};
+    void* c[2] = {nullptr, nullptr};
+    double* staging = nullptr;     // 3 N doubles, allocated on first host transfer
+    double* partials = nullptr;    // mass reduction scratch
+    double* mass_out = nullptr;    // 3 doubles
+    int mass_blocks = 0;
+    int cur = 0;
+    int64_t step = 0;
+    bool poisoned = false;
+    std::string err;
+    const Dispatch* ops = nullptr;
+};
+
+namespace {
+
+lbpf_status fail(lbpf_ctx* ctx, lbpf_status st, const std::string& msg) {
+    if (ctx) ctx->err = msg; else g_thread_error = msg;
+    return st;
+}
+
+lbpf_status cuda_fail(lbpf_ctx* ctx, cudaError_t e, const char* what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(ctx, e == cudaErrorMemoryAllocation ? LBPF_ENOMEM : LBPF_ECUDA, m);
+}
+
+#define LBPF_CUDA(ctx, call)                                    \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+// ---- per (lattice, storage) dispatch ---------------------------------------------
+
+struct Dispatch {
+    lbpf_status (*prepare)(lbpf_ctx*);
+    void (*launch_phi)(lbpf_ctx*, int cur);
+    void (*launch_c)(lbpf_ctx*, int cur);
+    void (*launch_init)(lbpf_ctx*);
+    void (*launch_pops_out)(lbpf_ctx*, double* g, double* h);
+};
+
+template <class L>
+struct TileCfg;
+template <>
+struct TileCfg<D2Q9> { static constexpr int BY = 8, BZ = 1; };
+template <>
+struct TileCfg<D3Q19> { static constexpr int BY = 4, BZ = 4; };
+
+template <class L, class SP>
+struct Impl {
+    using R = typename SP::real;
+    using S = typename SP::store_t;
+    static constexpr int BY = TileCfg<L>::BY, BZ = TileCfg<L>::BZ;
+    using T = Tile<L, BY, BZ>;
+    static constexpr size_t smem_phi = sizeof(R) * (T::N2 + (L::D + 2) * T::N1);
+    static constexpr size_t smem_c = sizeof(R) * (T::N2 + (L::D + 1) * T::N1);
+
+    static lbpf_status prepare(lbpf_ctx* ctx) {
+        LBPF_CUDA(ctx, cudaFuncSetAttribute(k_phi_step<L, SP, BY, BZ>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_phi));
+        LBPF_CUDA(ctx, cudaFuncSetAttribute(k_c_step<L, SP, BY, BZ>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
+        return LBPF_OK;
+    }
+    static dim3 grid(const lbpf_ctx* ctx) {
+        const StepParams& P = ctx->sp;
+        return dim3((P.nx + T::BX - 1) / T::BX, (P.ny + BY - 1) / BY, (P.nz + BZ - 1) / BZ);
+    }
+    static void launch_phi(lbpf_ctx* ctx, int cur) {
+        const int nxt = cur ^ 1;
+        k_phi_step<L, SP, BY, BZ><<<grid(ctx), dim3(T::BX, BY, BZ), smem_phi, ctx->stream>>>(
+            ctx->sp, (const S*)ctx->g[cur], (S*)ctx->g[nxt], (const R*)ctx->phi[cur], (const R*)ctx->c[cur],
+            (R*)ctx->phi[nxt]);
+    }
+    static void launch_c(lbpf_ctx* ctx, int cur) {
+        const int nxt = cur ^ 1;
+        k_c_step<L, SP, BY, BZ><<<grid(ctx), dim3(T::BX, BY, BZ), smem_c, ctx->stream>>>(
+            ctx->sp, (const S*)ctx->h[cur], (S*)ctx->h[nxt], (const R*)ctx->phi[cur], (const R*)ctx->phi[nxt],
+            (const R*)ctx->c[cur], (R*)ctx->c[nxt]);
+    }
+    static void launch_init(lbpf_ctx* ctx) {
+        const long long N = ctx->sp.N;
+        k_init<L, SP><<<(unsigned)((N + 255) / 256), 256, 0, ctx->stream>>>(
+            ctx->sp, (const R*)ctx->phi[ctx->cur], (const R*)ctx->c[ctx->cur], (S*)ctx->g[ctx->cur],
+            (S*)ctx->h[ctx->cur]);
+    }
+    static void launch_pops_out(lbpf_ctx* ctx, double* g, double* h) {
+        const long long N = ctx->sp.N;
+        const int cur = ctx->cur;
+        k_pops_out<L, SP><<<(unsigned)((N + 255) / 256), 256, 0, ctx->stream>>>(
+            ctx->sp, (const R*)ctx->phi[cur], (const R*)ctx->c[cur], (const S*)ctx->g[cur],
+            (const S*)ctx->h[cur], g, h);
+    }
+    static const Dispatch* table() {
+        static const Dispatch d = {prepare, launch_phi, launch_c, launch_init, launch_pops_out};
+        return &d;
+    }
+};
+
+const Dispatch* pick(int lattice, int precision) {
+    if (lattice == LBPF_D2Q9) {
+        switch (precision) {
+            case LBPF_FP64: return Impl<D2Q9, StoreF64>::table();
+            case LBPF_FP32: return Impl<D2Q9, StoreF32>::table();
+            case LBPF_FP32_BF16DEV: return Impl<D2Q9, StoreBF16Dev>::table();
+            case LBPF_FP32_FP16DEV: return Impl<D2Q9, StoreF16Dev>::table();
+        }
+    } else if (lattice == LBPF_D3Q19) {
+        switch (precision) {
+            case LBPF_FP64: return Impl<D3Q19, StoreF64>::table();
+            case LBPF_FP32: return Impl<D3Q19, StoreF32>::table();
+            case LBPF_FP32_BF16DEV: return Impl<D3Q19, StoreBF16Dev>::table();
+            case LBPF_FP32_FP16DEV: return Impl<D3Q19, StoreF16Dev>::table();
+        }
+    }
+    return nullptr;
+}
+
+lbpf_status validate(const lbpf_params* p, std::string& why) {
+    auto bad = [&](const char* m) { why = m; return LBPF_EINVAL; };
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) return bad("grid sizes must be >= 1");
+    if (p->lattice != LBPF_D2Q9 && p->lattice != LBPF_D3Q19) return bad("unknown lattice");
+    if (p->lattice == LBPF_D2Q9 && p->nz != 1) return bad("D2Q9 needs nz == 1");
+    if ((long long)p->nx * p->ny * p->nz > (1LL << 40)) return bad("grid too large");
+    for (int a = 0; a < 3; ++a) {
+        if (p->bc[a] != LBPF_PERIODIC && p->bc[a] != LBPF_BOUNCEBACK) return bad("unknown boundary type");
+        const int n = a == 0 ? p->nx : (a == 1 ? p->ny : p->nz);
+        const bool active = a < 2 || p->lattice == LBPF_D3Q19;
+        if (active && p->bc[a] == LBPF_BOUNCEBACK && n < 2) return bad("a bounce-back axis needs >= 2 nodes");
+    }
+    if (p->precision < LBPF_FP64 || p->precision > LBPF_FP32_FP16DEV) return bad("unknown precision");
+    if (!(p->dx > 0) || !(p->dt > 0)) return bad("dx and dt must be > 0");
+    if (!(p->tau_g > 0) || !(p->tau_h > 0)) return bad("tau_g and tau_h must be > 0");
+    if (!(p->W > 0)) return bad("W must be > 0");
+    if (!(p->D_l >= 0) || !(p->D_s >= 0)) return bad("diffusivities must be >= 0");
+    if (!std::isfinite(p->lambda) || !std::isfinite(p->c_s_co) || !std::isfinite(p->c_l_co) ||
+        !std::isfinite(p->mu_eq) || !std::isfinite(p->a_at) || !(p->eps_n >= 0))
+        return bad("non-finite parameter");
+    if (p->anti_trapping && p->a_at < 0 && !(p->D_l > 0)) return bad("automatic a needs D_l > 0");
+    return LBPF_OK;
+}
+
+StepParams lattice_units(const lbpf_params* p) {
+    StepParams s;
+    s.nx = p->nx; s.ny = p->ny; s.nz = p->nz;
+    for (int a = 0; a < 3; ++a) s.bc[a] = p->bc[a];
+    if (p->lattice == LBPF_D2Q9) s.bc[2] = LBPF_PERIODIC;
+    s.N = (long long)p->nx * p->ny * p->nz;
+    s.omg = 1.0 / (p->tau_g + 0.5);
+    s.omh = 1.0 / (p->tau_h + 0.5);
+    s.M = p->tau_g / 3.0;
+    s.gamma = 3.0 / p->tau_h;
+    const double dfac = p->dt / (p->dx * p->dx);
+    s.W = p->W / p->dx;
+    s.lambda = p->lambda;
+    s.D_l = p->D_l * dfac;
+    s.D_s = p->D_s * dfac;
+    s.c_s = p->c_s_co; s.c_l = p->c_l_co; s.mu_eq = p->mu_eq;
+    double a = p->a_at;
+    if (a < 0) a = 0.25 * (1.0 - p->D_s / p->D_l);
+    s.a_at = p->anti_trapping ? a : 0.0;
+    s.eps2 = p->eps_n * p->eps_n;
+    s.counter_term = p->counter_term ? 1 : 0;
+    return s;
+}
+
+void free_all(lbpf_ctx* ctx) {
+    for (int i = 0; i < 2; ++i) {
+        cudaFree(ctx->g[i]); cudaFree(ctx->h[i]); cudaFree(ctx->phi[i]); cudaFree(ctx->c[i]);
+        ctx->g[i] = ctx->h[i] = ctx->phi[i] = ctx->c[i] = nullptr;
+    }
+    cudaFree(ctx->staging); cudaFree(ctx->partials); cudaFree(ctx->mass_out);
+    ctx->staging = ctx->partials = ctx->mass_out = nullptr;
+}
+
+lbpf_status alloc(lbpf_ctx* ctx, void** ptr, size_t bytes, const char* what) {
+    if (const char* f = getenv("LBPF_FAULT")) {
+        if (strcmp(f, "alloc") == 0) return fail(ctx, LBPF_ENOMEM, std::string("injected allocation failure: ") + what);
+    }
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        cudaGetLastError();
+        return cuda_fail(ctx, e, what);
+    }
+    return LBPF_OK;
+}
+
+lbpf_status ensure_staging(lbpf_ctx* ctx) {
+    if (ctx->staging) return LBPF_OK;
+    return alloc(ctx, (void**)&ctx->staging, sizeof(double) * 3 * (size_t)ctx->sp.N, "staging");
+}
+
+lbpf_status check_launch(lbpf_ctx* ctx, const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, what);
+    return LBPF_OK;
+}
+
+template <typename R>
+void launch_from_f64(const double* src, void* dst, long long n, cudaStream_t s) {
+    k_from_f64<R><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, (R*)dst, n);
+}
+
+template <typename R>
+void launch_fields_out(lbpf_ctx* ctx, double* ophi, double* oc, double* omu) {
+    const long long N = ctx->sp.N;
+    k_fields_out<R><<<(unsigned)((N + 255) / 256), 256, 0, ctx->stream>>>(
+        ctx->sp, (const R*)ctx->phi[ctx->cur], (const R*)ctx->c[ctx->cur], ophi, oc, omu);
+}
+
+template <typename R>
+void launch_mass(lbpf_ctx* ctx) {
+    k_mass_partial<R><<<ctx->mass_blocks, kMassThreads, 0, ctx->stream>>>(
+        (const R*)ctx->c[ctx->cur], (const R*)ctx->phi[ctx->cur], ctx->sp.N, ctx->partials);
+    k_mass_final<<<1, kMassThreads, 0, ctx->stream>>>(ctx->partials, ctx->mass_blocks, ctx->mass_out);
+}
+
+bool is_f64(const lbpf_ctx* ctx) { return ctx->p.precision == LBPF_FP64; }
+
+}  // namespace
+
+// ==== C ABI ======================================================================
+
+extern "C" {
+
+lbpf_status lbpf_default_params(lbpf_params* p) {
+    if (!p) return fail(nullptr, LBPF_EINVAL, "params pointer is NULL");
+    memset(p, 0, sizeof(*p));
+    p->nx = 64; p->ny = 64; p->nz = 1;
+    p->lattice = LBPF_D2Q9;
+    p->precision = LBPF_FP64;
+    p->dx = 1.0; p->dt = 1.0;
+    p->tau_g = 0.36; p->tau_h = 0.36;
+    p->W = 3.0; p->lambda = 0.0;
+    p->D_l = 0.1; p->D_s = 0.1;
+    p->c_s_co = 1.0; p->c_l_co = 0.5; p->mu_eq = 0.4;
+    p->counter_term = 1; p->anti_trapping = 0; p->a_at = -1.0;
+    p->eps_n = 1e-12;
+    return LBPF_OK;
+}
+
+lbpf_status lbpf_create(const lbpf_params* p, const double* phi0, const double* c0, int32_t ptr_is_device,
+                        void* cuda_stream, lbpf_ctx** out) {
+    if (!out) return fail(nullptr, LBPF_EINVAL, "out pointer is NULL");
+    *out = nullptr;
+    if (!p || !phi0 || !c0) return fail(nullptr, LBPF_EINVAL, "NULL params or field pointer");
+    std::string why;
+    if (validate(p, why) != LBPF_OK) return fail(nullptr, LBPF_EINVAL, why);
+    const Dispatch* ops = pick(p->lattice, p->precision);
+    if (!ops) return fail(nullptr, LBPF_EUNSUPPORTED, "lattice/precision not built");
+
+    lbpf_ctx* ctx = new (std::nothrow) lbpf_ctx();
+    if (!ctx) return fail(nullptr, LBPF_ENOMEM, "host allocation failed");
+    ctx->p = *p;
+    ctx->sp = lattice_units(p);
+    ctx->q = p->lattice == LBPF_D3Q19 ? 19 : 9;
+    ctx->ops = ops;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    ctx->real_size = p->precision == LBPF_FP64 ? 8 : 4;
+    ctx->store_size = p->precision == LBPF_FP64 ? 8 : (p->precision == LBPF_FP32 ? 4 : 2);
+    const size_t N = (size_t)ctx->sp.N;
+
+    auto abort_create = [&](lbpf_status st) {
+        std::string m = ctx->err;
+        free_all(ctx);
+        delete ctx;
+        g_thread_error = m;
+        return st;
+    };
+    lbpf_status st;
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e != cudaSuccess) { cuda_fail(ctx, e, "cudaGetDevice"); return abort_create(LBPF_ECUDA); }
+    for (int i = 0; i < 2; ++i) {
+        if ((st = alloc(ctx, &ctx->g[i], ctx->store_size * ctx->q * N, "g populations")) != LBPF_OK) return abort_create(st);
+        if ((st = alloc(ctx, &ctx->h[i], ctx->store_size * ctx->q * N, "h populations")) != LBPF_OK) return abort_create(st);
+        if ((st = alloc(ctx, &ctx->phi[i], ctx->real_size * N, "phi field")) != LBPF_OK) return abort_create(st);
+        if ((st = alloc(ctx, &ctx->c[i], ctx->real_size * N, "c field")) != LBPF_OK) return abort_create(st);
+    }
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    const long long want = (ctx->sp.N + kMassThreads - 1) / kMassThreads;
+    ctx->mass_blocks = (int)std::min<long long>(want, 4LL * sms);
+    if (ctx->mass_blocks < 1) ctx->mass_blocks = 1;
+    if ((st = alloc(ctx, (void**)&ctx->partials, sizeof(double) * 3 * ctx->mass_blocks, "mass partials")) != LBPF_OK) return abort_create(st);
+    if ((st = alloc(ctx, (void**)&ctx->mass_out, sizeof(double) * 3, "mass result")) != LBPF_OK) return abort_create(st);
+    if ((st = ops->prepare(ctx)) != LBPF_OK) return abort_create(st);
+
+    const double* sphi = phi0;
+    const double* sc = c0;
+    if (!ptr_is_device) {
+        if ((st = ensure_staging(ctx)) != LBPF_OK) return abort_create(st);
+        e = cudaMemcpyAsync(ctx->staging, phi0, sizeof(double) * N, cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ctx->staging + N, c0, sizeof(double) * N, cudaMemcpyHostToDevice, ctx->stream);
+        if (e != cudaSuccess) { cuda_fail(ctx, e, "copy of phi0/c0"); return abort_create(LBPF_ECUDA); }
+        sphi = ctx->staging;
+        sc = ctx->staging + N;
+    }
+    if (is_f64(ctx)) {
+        launch_from_f64<double>(sphi, ctx->phi[0], (long long)N, ctx->stream);
+        launch_from_f64<double>(sc, ctx->c[0], (long long)N, ctx->stream);
+    } else {
+        launch_from_f64<float>(sphi, ctx->phi[0], (long long)N, ctx->stream);
+        launch_from_f64<float>(sc, ctx->c[0], (long long)N, ctx->stream);
+    }
+    ctx->cur = 0;
+    ops->launch_init(ctx);
+    if ((st = check_launch(ctx, "initialisation kernels")) != LBPF_OK) return abort_create(st);
+    e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) { cuda_fail(ctx, e, "initialisation"); return abort_create(LBPF_ECUDA); }
+    *out = ctx;
+    return LBPF_OK;
+}
+
+lbpf_status lbpf_step(lbpf_ctx* ctx, int64_t nsteps) {
+    if (!ctx) return fail(nullptr, LBPF_EINVAL, "ctx is NULL");
+    if (ctx->poisoned) return fail(ctx, LBPF_ESTATE, "context poisoned by an earlier error");
+    if (nsteps < 0) return fail(ctx, LBPF_EINVAL, "nsteps < 0");
+    for (int64_t s = 0; s < nsteps; ++s) {
+        ctx->ops->launch_phi(ctx, ctx->cur);
+        ctx->ops->launch_c(ctx, ctx->cur);
+        ctx->cur ^= 1;
+        ctx->step += 1;
+    }
+    return check_launch(ctx, "step kernels");
+}
+
+lbpf_status lbpf_step_timed(lbpf_ctx* ctx, int64_t nsteps, double* kernel_ms) {
+    if (!ctx) return fail(nullptr, LBPF_EINVAL, "ctx is NULL");
+    if (ctx->poisoned) return fail(ctx, LBPF_ESTATE, "context poisoned by an earlier error");
+    if (nsteps < 0 || !kernel_ms) return fail(ctx, LBPF_EINVAL, "nsteps < 0 or kernel_ms NULL");
+    kernel_ms[0] = kernel_ms[1] = 0.0;
+    if (nsteps == 0) return LBPF_OK;
+    std::vector<cudaEvent_t> ev(3 * nsteps, nullptr);
+    lbpf_status st = LBPF_OK;
+    for (auto& x : ev) {
+        cudaError_t e = cudaEventCreate(&x);
+        if (e != cudaSuccess) { st = cuda_fail(ctx, e, "cudaEventCreate"); break; }
+    }
+    if (st == LBPF_OK) {
+        for (int64_t s = 0; s < nsteps; ++s) {
+            cudaEventRecord(ev[3 * s], ctx->stream);
+            ctx->ops->launch_phi(ctx, ctx->cur);
+            cudaEventRecord(ev[3 * s + 1], ctx->stream);
+            ctx->ops->launch_c(ctx, ctx->cur);
+            cudaEventRecord(ev[3 * s + 2], ctx->stream);
+            ctx->cur ^= 1;
+            ctx->step += 1;
+        }
+        st = check_launch(ctx, "step kernels");
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (st == LBPF_OK && e != cudaSuccess) st = cuda_fail(ctx, e, "step synchronisation");
+        for (int64_t s = 0; st == LBPF_OK && s < nsteps; ++s) {
+            float a = 0.f, b = 0.f;
+            cudaEventElapsedTime(&a, ev[3 * s], ev[3 * s + 1]);
+            cudaEventElapsedTime(&b, ev[3 * s + 1], ev[3 * s + 2]);
+            kernel_ms[0] += a;
+            kernel_ms[1] += b;
+        }
+    }
+    for (auto& x : ev) if (x) cudaEventDestroy(x);
+    return st;
+}
+
+lbpf_status lbpf_mass(lbpf_ctx* ctx, double* total_c, double* total_phi) {
+    if (!ctx) return fail(nullptr, LBPF_EINVAL, "ctx is NULL");
+    if (ctx->poisoned) return fail(ctx, LBPF_ESTATE, "context poisoned by an earlier error");
+    if (is_f64(ctx)) launch_mass<double>(ctx); else launch_mass<float>(ctx);
+    lbpf_status st = check_launch(ctx, "mass kernels");
+    if (st != LBPF_OK) return st;
+    double hostv[3];
+    LBPF_CUDA(ctx, cudaMemcpyAsync(hostv, ctx->mass_out, sizeof(hostv), cudaMemcpyDeviceToHost, ctx->stream));
+    LBPF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (total_c) *total_c = hostv[0];
+    if (total_phi) *total_phi = hostv[1];
+    if (hostv[2] != 0.0 || !std::isfinite(hostv[0]) || !std::isfinite(hostv[1])) {
+        ctx->poisoned = true;
+        char buf[160];
+        snprintf(buf, sizeof(buf), "unstable: %.0f node(s) non-finite or with phi outside [-0.5, 1.5] at step %lld",
+                 hostv[2], (long long)ctx->step);
+        return fail(ctx, LBPF_EUNSTABLE, buf);
+    }
+    return LBPF_OK;
+}
+
+lbpf_status lbpf_get_fields(lbpf_ctx* ctx, double* phi, double* c, double* mu, int32_t ptr_is_device) {
+    if (!ctx) return fail(nullptr, LBPF_EINVAL, "ctx is NULL");
+    if (ctx->poisoned) return fail(ctx, LBPF_ESTATE, "context poisoned by an earlier error");
+    const size_t N = (size_t)ctx->sp.N;
+    double *dphi = phi, *dc = c, *dmu = mu;
+    if (!ptr_is_device) {
+        lbpf_status st = ensure_staging(ctx);
+        if (st != LBPF_OK) return st;
+        dphi = phi ? ctx->staging : nullptr;
+        dc = c ? ctx->staging + N : nullptr;
+        dmu = mu ? ctx->staging + 2 * N : nullptr;
+    }
+    if (is_f64(ctx)) launch_fields_out<double>(ctx, dphi, dc, dmu);
+    else launch_fields_out<float>(ctx, dphi, dc, dmu);
+    lbpf_status st = check_launch(ctx, "field export kernel");
+    if (st != LBPF_OK) return st;
+    if (!ptr_is_device) {
+        if (phi) LBPF_CUDA(ctx, cudaMemcpyAsync(phi, dphi, sizeof(double) * N, cudaMemcpyDeviceToHost, ctx->stream));
+        if (c) LBPF_CUDA(ctx, cudaMemcpyAsync(c, dc, sizeof(double) * N, cudaMemcpyDeviceToHost, ctx->stream));
+        if (mu) LBPF_CUDA(ctx, cudaMemcpyAsync(mu, dmu, sizeof(double) * N, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    LBPF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return LBPF_OK;
+}
+
+lbpf_status lbpf_get_populations(lbpf_ctx* ctx, double* g, double* h, int32_t ptr_is_device) {
+    if (!ctx) return fail(nullptr, LBPF_EINVAL, "ctx is NULL");
+    if (ctx->poisoned) return fail(ctx, LBPF_ESTATE, "context poisoned by an earlier error");
+    const size_t bytes = sizeof(double) * ctx->q * (size_t)ctx->sp.N;
+    double *dg = g, *dh = h, *tmp = nullptr;
+    if (!ptr_is_device && (g || h)) {
+        lbpf_status st = alloc(ctx, (void**)&tmp, 2 * bytes, "population export buffer");
+        if (st != LBPF_OK) return st;
+        dg = g ? tmp : nullptr;
+        dh = h ? tmp + ctx->q * (size_t)ctx->sp.N : nullptr;
+    }
+    ctx->ops->launch_pops_out(ctx, dg, dh);
+    lbpf_status st = check_launch(ctx, "population export kernel");
+    cudaError_t e = cudaSuccess;
+    if (st == LBPF_OK && !ptr_is_device) {
+        if (g && e == cudaSuccess) e = cudaMemcpyAsync(g, dg, bytes, cudaMemcpyDeviceToHost, ctx->stream);
+        if (h && e == cudaSuccess) e = cudaMemcpyAsync(h, dh, bytes, cudaMemcpyDeviceToHost, ctx->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (tmp) cudaFree(tmp);
+    if (st == LBPF_OK && e != cudaSuccess) st = cuda_fail(ctx, e, "population export");
+    return st;
+}
+
+lbpf_status lbpf_get_step(const lbpf_ctx* ctx, int64_t* step) {
+    if (!ctx || !step) return fail(nullptr, LBPF_EINVAL, "NULL argument");
+    *step = ctx->step;
+    return LBPF_OK;
+}
+
+lbpf_status lbpf_destroy(lbpf_ctx* ctx) {
+    if (!ctx) return LBPF_OK;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream); else cudaDeviceSynchronize();
+    free_all(ctx);
+    delete ctx;
+    return LBPF_OK;
+}
+
+const char* lbpf_last_error(const lbpf_ctx* ctx) {
+    return ctx ? ctx->err.c_str() : g_thread_error.c_str();
+}
+
+lbpf_status lbpf_lattice_info(int32_t lattice, int32_t* q, int32_t* e, double* w) {
+    if (!q) return fail(nullptr, LBPF_EINVAL, "q is NULL");
+    if (lattice == LBPF_D2Q9) {
+        *q = 9;
+        for (int k = 0; k < 9; ++k) {
+            if (e) { e[3 * k] = D2Q9::ex(k); e[3 * k + 1] = D2Q9::ey(k); e[3 * k + 2] = 0; }
+            if (w) w[k] = D2Q9::w(k);
+        }
+    } else if (lattice == LBPF_D3Q19) {
+        *q = 19;
+        for (int k = 0; k < 19; ++k) {
+            if (e) { e[3 * k] = D3Q19::ex(k); e[3 * k + 1] = D3Q19::ey(k); e[3 * k + 2] = D3Q19::ez(k); }
+            if (w) w[k] = D3Q19::w(k);
+        }
+    } else {
+        return fail(nullptr, LBPF_EINVAL, "unknown lattice");
+    }
+    return LBPF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,250 @@
+"""Thin ctypes binding of libgb_lbpf (include/lbpf.h), same names as the C ABI.
+
+Argument marshalling only: every step of the method runs in the library's CUDA
+kernels.  Host arrays are numpy float64 (C order); device arrays are anything
+with ``data_ptr()`` (a CUDA torch tensor, float64, contiguous).  There is no CPU
+fallback: if the library is missing, loading fails with an error that says how
+to build it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import fields as dc_fields
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgb_lbpf.so")
+
+LBPF_OK, LBPF_EINVAL, LBPF_ENOMEM, LBPF_ECUDA, LBPF_EUNSTABLE, LBPF_ETIMEOUT, LBPF_ESTATE, \
+    LBPF_EUNSUPPORTED = range(8)
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EUNSTABLE", "ETIMEOUT", "ESTATE", "EUNSUPPORTED"]
+LBPF_D2Q9, LBPF_D3Q19 = 0, 1
+LBPF_FP64, LBPF_FP32, LBPF_FP32_BF16DEV, LBPF_FP32_FP16DEV = 0, 1, 2, 3
+PRECISIONS = {"fp64": LBPF_FP64, "fp32": LBPF_FP32, "bf16dev": LBPF_FP32_BF16DEV,
+              "fp16dev": LBPF_FP32_FP16DEV}
+
+
+class LbpfError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__("LBPF_%s: %s" % (name, message))
+
+
+class lbpf_params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("lattice", ctypes.c_int32), ("bc", ctypes.c_int32 * 3),
+                ("precision", ctypes.c_int32), ("dx", ctypes.c_double), ("dt", ctypes.c_double),
+                ("tau_g", ctypes.c_double), ("tau_h", ctypes.c_double), ("W", ctypes.c_double),
+                ("lambda_", ctypes.c_double), ("D_l", ctypes.c_double), ("D_s", ctypes.c_double),
+                ("c_s_co", ctypes.c_double), ("c_l_co", ctypes.c_double),
+                ("mu_eq", ctypes.c_double), ("counter_term", ctypes.c_int32),
+                ("anti_trapping", ctypes.c_int32), ("a_at", ctypes.c_double),
+                ("eps_n", ctypes.c_double), ("mass_every", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+_vp = ctypes.c_void_p
+
+
+def load() -> ctypes.CDLL:
+    """Load libgb_lbpf.so (built in-tree by __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libgb_lbpf.so is not built (%s); run "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    st = ctypes.c_int
+    sig = {
+        "lbpf_default_params": [ctypes.POINTER(lbpf_params)],
+        "lbpf_create": [ctypes.POINTER(lbpf_params), _vp, _vp, ctypes.c_int32, _vp,
+                        ctypes.POINTER(_vp)],
+        "lbpf_step": [_vp, ctypes.c_int64],
+        "lbpf_step_timed": [_vp, ctypes.c_int64, _dp],
+        "lbpf_mass": [_vp, _dp, _dp],
+        "lbpf_get_fields": [_vp, _vp, _vp, _vp, ctypes.c_int32],
+        "lbpf_get_populations": [_vp, _vp, _vp, ctypes.c_int32],
+        "lbpf_get_step": [_vp, ctypes.POINTER(ctypes.c_int64)],
+        "lbpf_destroy": [_vp],
+        "lbpf_lattice_info": [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                              ctypes.POINTER(ctypes.c_int32), _dp],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = st
+    lib.lbpf_last_error.argtypes = [_vp]
+    lib.lbpf_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    """Names declared in include/lbpf.h that the loaded library must export."""
+    return ["lbpf_default_params", "lbpf_create", "lbpf_step", "lbpf_step_timed", "lbpf_mass",
+            "lbpf_get_fields", "lbpf_get_populations", "lbpf_get_step", "lbpf_destroy",
+            "lbpf_last_error", "lbpf_lattice_info"]
+
+
+def _check(status: int, ctx=None):
+    if status != LBPF_OK:
+        msg = load().lbpf_last_error(ctx)
+        raise LbpfError(status, msg.decode() if msg else "")
+
+
+def _ptr(a):
+    """(address, is_device) of a numpy array or a CUDA tensor; None -> (None, None)."""
+    if a is None:
+        return None, None
+    if hasattr(a, "data_ptr"):
+        if a.dtype.__str__() != "torch.float64" or not a.is_contiguous():
+            raise ValueError("device arrays must be contiguous float64")
+        return a.data_ptr(), bool(a.is_cuda)
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+        raise ValueError("host arrays must be C-contiguous float64 numpy arrays")
+    return a.ctypes.data, False
+
+
+# ---- the ABI, one function per C entry point ---------------------------------------
+
+def lbpf_default_params() -> lbpf_params:
+    p = lbpf_params()
+    _check(load().lbpf_default_params(ctypes.byref(p)))
+    return p
+
+
+def lbpf_create(p: lbpf_params, phi0, c0, ptr_is_device: int, cuda_stream=None):
+    ctx = _vp()
+    a, _ = _ptr(phi0)
+    b, _ = _ptr(c0)
+    _check(load().lbpf_create(ctypes.byref(p), a, b, int(ptr_is_device), cuda_stream or None,
+                              ctypes.byref(ctx)))
+    return ctx
+
+
+def lbpf_step(ctx, nsteps: int) -> None:
+    _check(load().lbpf_step(ctx, int(nsteps)), ctx)
+
+
+def lbpf_step_timed(ctx, nsteps: int):
+    ms = (ctypes.c_double * 2)()
+    _check(load().lbpf_step_timed(ctx, int(nsteps), ms), ctx)
+    return float(ms[0]), float(ms[1])
+
+
+def lbpf_mass(ctx):
+    tc, tp = ctypes.c_double(), ctypes.c_double()
+    _check(load().lbpf_mass(ctx, ctypes.byref(tc), ctypes.byref(tp)), ctx)
+    return tc.value, tp.value
+
+
+def lbpf_get_fields(ctx, phi=None, c=None, mu=None, ptr_is_device: int = 0) -> None:
+    _check(load().lbpf_get_fields(ctx, _ptr(phi)[0], _ptr(c)[0], _ptr(mu)[0], int(ptr_is_device)), ctx)
+
+
+def lbpf_get_populations(ctx, g=None, h=None, ptr_is_device: int = 0) -> None:
+    _check(load().lbpf_get_populations(ctx, _ptr(g)[0], _ptr(h)[0], int(ptr_is_device)), ctx)
+
+
+def lbpf_get_step(ctx) -> int:
+    s = ctypes.c_int64()
+    _check(load().lbpf_get_step(ctx, ctypes.byref(s)), ctx)
+    return s.value
+
+
+def lbpf_destroy(ctx) -> None:
+    if ctx:
+        load().lbpf_destroy(ctx)
+
+
+def lbpf_last_error(ctx=None) -> str:
+    m = load().lbpf_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def lbpf_lattice_info(lattice: int):
+    q = ctypes.c_int32()
+    e = (ctypes.c_int32 * 57)()
+    w = np.zeros(19)
+    _check(load().lbpf_lattice_info(int(lattice), ctypes.byref(q), e, w.ctypes.data_as(_dp)))
+    n = q.value
+    return np.array(e[:3 * n], dtype=np.int64).reshape(n, 3), w[:n].copy()
+
+
+# ---- convenience wrapper -------------------------------------------------------------
+
+def params_from(model, precision="fp64", dx=1.0, dt=1.0) -> lbpf_params:
+    """lbpf_params from a workloads.ModelParams (lattice units unless dx, dt given)."""
+    p = lbpf_default_params()
+    p.nx, p.ny, p.nz = model.nx, model.ny, model.nz
+    p.lattice = LBPF_D3Q19 if model.nz > 1 else LBPF_D2Q9
+    for a in range(3):
+        p.bc[a] = int(model.bc[a])
+    p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    p.dx, p.dt = dx, dt
+    p.tau_g, p.tau_h, p.W, p.lambda_ = model.tau_g, model.tau_h, model.W, model.lam
+    p.D_l, p.D_s = model.D_l, model.D_s
+    p.c_s_co, p.c_l_co, p.mu_eq = model.c_s_co, model.c_l_co, model.mu_eq
+    p.counter_term, p.anti_trapping = int(model.counter_term), int(model.anti_trapping)
+    p.a_at, p.eps_n = model.a_at, model.eps_n
+    return p
+
+
+class Simulation:
+    """One GPU simulation context.  Host fields in/out are numpy float64 arrays
+    shaped (nz, ny, nx); device fields are CUDA float64 tensors."""
+
+    def __init__(self, model, phi0, c0, precision="fp64", stream=None, lattice=None):
+        self.model = model
+        self.params = params_from(model, precision)
+        if lattice is not None:
+            self.params.lattice = int(lattice)
+        is_dev = hasattr(phi0, "data_ptr")
+        if not is_dev:
+            phi0 = np.ascontiguousarray(phi0, dtype=np.float64)
+            c0 = np.ascontiguousarray(c0, dtype=np.float64)
+        self.ctx = lbpf_create(self.params, phi0, c0, int(is_dev), stream)
+        self.q = 19 if self.params.lattice == LBPF_D3Q19 else 9
+        self.shape = (model.nz, model.ny, model.nx)
+
+    def step(self, n=1):
+        lbpf_step(self.ctx, n)
+        return self
+
+    def step_timed(self, n):
+        return lbpf_step_timed(self.ctx, n)
+
+    def mass(self):
+        return lbpf_mass(self.ctx)
+
+    def fields(self):
+        phi, c, mu = (np.empty(self.shape) for _ in range(3))
+        lbpf_get_fields(self.ctx, phi, c, mu, 0)
+        return phi, c, mu
+
+    def populations(self):
+        g = np.empty((self.q,) + self.shape)
+        h = np.empty((self.q,) + self.shape)
+        lbpf_get_populations(self.ctx, g, h, 0)
+        return g, h
+
+    @property
+    def t(self):
+        return lbpf_get_step(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            lbpf_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,132 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Metric (infinity norm): max_x |gpu - oracle| / max_x |oracle|, per field and per
+population plane.  FP64 must agree to 1e-11 after 100 steps; the FP32 and 16-bit
+storage modes state their error against the FP64 oracle with the bounds below.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2111_05960_gb300 import lbpf as L
+from paper_2111_05960_gb300 import workloads as WL
+from conftest import rel_err, to_oracle
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-11
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2111_05960_gb300 import build as B
+    B.build()
+    L.load()
+
+
+def _case(shape, seed, **kw):
+    nz, ny, nx = shape
+    base = dict(tau_g=0.7, tau_h=0.9, W=3.0, lam=4.0, D_l=0.15, D_s=0.03,
+                counter_term=1, anti_trapping=1, a_at=0.2)
+    base.update(kw)
+    m = WL.ModelParams(nx=nx, ny=ny, nz=nz, **base)
+    phi0, c0 = WL.random_fields(shape, seed=seed)
+    return m, phi0, c0
+
+
+def _compare(m, phi0, c0, steps, precision="fp64", pops=True):
+    sim = L.Simulation(m, phi0, c0, precision=precision)
+    sim.step(steps)
+    phi, c, mu = sim.fields()
+    g, h = sim.populations() if pops else (None, None)
+    sim.close()
+    o = O.Oracle(to_oracle(m), phi0, c0).step(steps)
+    errs = dict(phi=rel_err(phi, o.phi), c=rel_err(c, o.c), mu=rel_err(mu, o.mu))
+    if pops:
+        errs["g"] = max(rel_err(g[k], o.g[k]) for k in range(g.shape[0]))
+        errs["h"] = max(rel_err(h[k], o.h[k]) for k in range(h.shape[0]))
+    return errs
+
+
+# 2-D shapes span several 32x8 tiles with ragged tails, plus degenerate 1-wide axes
+@pytest.mark.parametrize("shape,bc,ct,at", [
+    ((1, 21, 70), (0, 0, 0), 1, 1),
+    ((1, 21, 70), (1, 0, 0), 0, 1),
+    ((1, 17, 33), (1, 1, 0), 1, 0),
+    ((1, 8, 64), (0, 1, 0), 0, 0),
+    ((1, 1, 40), (0, 0, 0), 1, 1),
+    ((1, 9, 2), (1, 0, 0), 1, 1),
+])
+def test_fp64_2d_matches_oracle(shape, bc, ct, at):
+    m, phi0, c0 = _case(shape, seed=sum(shape) + ct, bc=bc, counter_term=ct, anti_trapping=at)
+    errs = _compare(m, phi0, c0, 100)
+    assert max(errs.values()) < FP64_TOL, errs
+
+
+@pytest.mark.parametrize("shape,bc,ct", [
+    ((9, 11, 37), (0, 0, 0), 1),
+    ((6, 10, 33), (1, 0, 1), 0),
+    ((5, 4, 40), (1, 1, 1), 1),
+    ((2, 6, 35), (0, 0, 0), 1),
+])
+def test_fp64_3d_matches_oracle(shape, bc, ct):
+    m, phi0, c0 = _case(shape, seed=3 * sum(shape) + ct, bc=bc, counter_term=ct)
+    m_lat = L.LBPF_D3Q19
+    sim = L.Simulation(m, phi0, c0, precision="fp64", lattice=m_lat)
+    sim.step(50)
+    phi, c, mu = sim.fields()
+    g, h = sim.populations()
+    sim.close()
+    o = O.Oracle(to_oracle(m), phi0, c0).step(50)
+    errs = dict(phi=rel_err(phi, o.phi), c=rel_err(c, o.c), mu=rel_err(mu, o.mu),
+                g=max(rel_err(g[k], o.g[k]) for k in range(19)),
+                h=max(rel_err(h[k], o.h[k]) for k in range(19)))
+    assert max(errs.values()) < FP64_TOL, errs
+
+
+def test_planar_front_config_fp64_2000_steps():
+    """512 x 8 planar dissolution, walls in x, y periodic, 2000 steps."""
+    m, phi0, c0 = WL.planar_1d()
+    errs = _compare(m, phi0, c0, 2000, pops=False)
+    assert max(errs.values()) < FP64_TOL, errs
+
+
+def test_disc_config_fp64_counter_term_on_and_off():
+    """512 x 512 periodic disc, R = 60, W = 3, D_l = D_s = 0.05, both phi equations."""
+    for ct in (1, 0):
+        m, phi0, c0 = WL.disc_2d(counter_term=ct, equilibrium=False)
+        errs = _compare(m, phi0, c0, 100, pops=False)
+        assert max(errs.values()) < FP64_TOL, (ct, errs)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 2e-5)])
+def test_reduced_precision_error_against_fp64_oracle(precision, tol):
+    m, phi0, c0 = WL.disc_2d(n=128, R=30.0, counter_term=1, equilibrium=False)
+    errs = _compare(m, phi0, c0, 200, precision=precision, pops=False)
+    assert errs["phi"] < tol and errs["c"] < tol, errs
+
+
+def test_fp64_mass_is_conserved_on_gpu():
+    m, phi0, c0 = _case((1, 40, 96), seed=9, bc=(1, 0, 0))
+    sim = L.Simulation(m, phi0, c0, precision="fp64")
+    m0, _ = sim.mass()
+    sim.step(500)
+    m1, _ = sim.mass()
+    sim.close()
+    assert abs(m1 - m0) / m0 < 1e-13
+    assert abs(m0 - c0.sum()) / c0.sum() < 1e-14
+
+
+def test_device_pointers_roundtrip():
+    import torch
+    m, phi0, c0 = _case((1, 16, 40), seed=2)
+    dphi = torch.tensor(phi0, dtype=torch.float64, device="cuda")
+    dc = torch.tensor(c0, dtype=torch.float64, device="cuda")
+    sim = L.Simulation(m, dphi, dc, precision="fp64")
+    sim.step(10)
+    out = torch.empty_like(dphi)
+    L.lbpf_get_fields(sim.ctx, out, None, None, 1)
+    torch.cuda.synchronize()
+    o = O.Oracle(to_oracle(m), phi0, c0).step(10)
+    sim.close()
+    assert rel_err(out.cpu().numpy(), o.phi) < FP64_TOL
