@@ -28,8 +28,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     nvcc = os.environ.get("NVCC", "nvcc")
     tmp = LIB + ".%d.tmp" % os.getpid()
+    extra = os.environ.get("LBPF_NVCC_FLAGS", "").split()
     cmd = [nvcc, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
-           "-I" + INCLUDE, "-I" + CSRC, "-o", tmp] + [os.path.join(CSRC, s) for s in SOURCES]
+           "-I" + INCLUDE, "-I" + CSRC, *extra, "-o", tmp] + [os.path.join(CSRC, s) for s in SOURCES]
     if verbose:
         print(" ".join(cmd), file=sys.stderr)
     subprocess.check_call(cmd)

@@ -29,6 +29,7 @@ struct Dispatch;
 struct lbpf_ctx {
     lbpf_params p;
     StepParams sp;
+    KParams kp;
     int q = 0;
     size_t real_size = 0, store_size = 0;
     cudaStream_t stream = nullptr;
@@ -76,56 +77,90 @@ struct Dispatch {
     void (*launch_pops_out)(lbpf_ctx*, double* g, double* h);
 };
 
+// Tile shapes: 32 x BY threads per block, ZCH planes per block in 3-D, at least
+// MINB resident blocks per SM (register budget).  Overridable at build time.
+#ifndef LBPF_BY2
+#define LBPF_BY2 8
+#endif
+#ifndef LBPF_MINB2
+#define LBPF_MINB2 2
+#endif
+#ifndef LBPF_BY3
+#define LBPF_BY3 8
+#endif
+#ifndef LBPF_ZCH3
+#define LBPF_ZCH3 16
+#endif
+#ifndef LBPF_MINB3
+#define LBPF_MINB3 3
+#endif
+#ifndef LBPF_MINB3_F64
+#define LBPF_MINB3_F64 2
+#endif
 template <class L>
 struct TileCfg;
 template <>
-struct TileCfg<D2Q9> { static constexpr int BY = 8, BZ = 1; };
+struct TileCfg<D2Q9> { static constexpr int BY = LBPF_BY2, ZCH = 1, MINB = LBPF_MINB2; };
 template <>
-struct TileCfg<D3Q19> { static constexpr int BY = 4, BZ = 4; };
+struct TileCfg<D3Q19> { static constexpr int BY = LBPF_BY3, ZCH = LBPF_ZCH3, MINB = LBPF_MINB3; };
+template <class L, class SP>
+constexpr int min_blocks() {
+    return (L::D == 3 && sizeof(typename SP::real) == 8) ? LBPF_MINB3_F64 : TileCfg<L>::MINB;
+}
 
 template <class L, class SP>
 struct Impl {
     using R = typename SP::real;
     using S = typename SP::store_t;
-    static constexpr int BY = TileCfg<L>::BY, BZ = TileCfg<L>::BZ;
-    using T = Tile<L, BY, BZ>;
-    static constexpr size_t smem_phi = sizeof(R) * (T::N2 + (L::D + 2) * T::N1);
-    static constexpr size_t smem_c = sizeof(R) * (T::N2 + (L::D + 1) * T::N1);
+    static constexpr int BY = TileCfg<L>::BY, ZCH = TileCfg<L>::ZCH, MINB = min_blocks<L, SP>();
+    static constexpr size_t smem_phi = march_smem<L, SP, BY, ZCH>(true);
+    static constexpr size_t smem_c = march_smem<L, SP, BY, ZCH>(false);
 
     static lbpf_status prepare(lbpf_ctx* ctx) {
-        LBPF_CUDA(ctx, cudaFuncSetAttribute(k_phi_step<L, SP, BY, BZ>,
+        LBPF_CUDA(ctx, cudaFuncSetAttribute(k_phi_step<L, SP, BY, ZCH, MINB, true>,
                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_phi));
-        LBPF_CUDA(ctx, cudaFuncSetAttribute(k_c_step<L, SP, BY, BZ>,
+        LBPF_CUDA(ctx, cudaFuncSetAttribute(k_c_step<L, SP, BY, ZCH, MINB, true>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
+        LBPF_CUDA(ctx, cudaFuncSetAttribute(k_phi_step<L, SP, BY, ZCH, MINB, false>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_phi));
+        LBPF_CUDA(ctx, cudaFuncSetAttribute(k_c_step<L, SP, BY, ZCH, MINB, false>,
                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
         return LBPF_OK;
     }
+    static bool walls(const lbpf_ctx* ctx) {
+        const StepParams& P = ctx->sp;
+        return P.bc[0] || P.bc[1] || (L::D == 3 && P.bc[2]);
+    }
     static dim3 grid(const lbpf_ctx* ctx) {
         const StepParams& P = ctx->sp;
-        return dim3((P.nx + T::BX - 1) / T::BX, (P.ny + BY - 1) / BY, (P.nz + BZ - 1) / BZ);
+        const int zblocks = L::D == 3 ? (P.nz + ZCH - 1) / ZCH : 1;
+        return dim3((P.nx + 31) / 32, (P.ny + BY - 1) / BY, zblocks);
     }
     static void launch_phi(lbpf_ctx* ctx, int cur) {
         const int nxt = cur ^ 1;
-        k_phi_step<L, SP, BY, BZ><<<grid(ctx), dim3(T::BX, BY, BZ), smem_phi, ctx->stream>>>(
-            ctx->sp, (const S*)ctx->g[cur], (S*)ctx->g[nxt], (const R*)ctx->phi[cur], (const R*)ctx->c[cur],
+        auto kern = walls(ctx) ? k_phi_step<L, SP, BY, ZCH, MINB, true> : k_phi_step<L, SP, BY, ZCH, MINB, false>;
+        kern<<<grid(ctx), dim3(32, BY), smem_phi, ctx->stream>>>(
+            ctx->kp, (const S*)ctx->g[cur], (S*)ctx->g[nxt], (const R*)ctx->phi[cur], (const R*)ctx->c[cur],
             (R*)ctx->phi[nxt]);
     }
     static void launch_c(lbpf_ctx* ctx, int cur) {
         const int nxt = cur ^ 1;
-        k_c_step<L, SP, BY, BZ><<<grid(ctx), dim3(T::BX, BY, BZ), smem_c, ctx->stream>>>(
-            ctx->sp, (const S*)ctx->h[cur], (S*)ctx->h[nxt], (const R*)ctx->phi[cur], (const R*)ctx->phi[nxt],
+        auto kern = walls(ctx) ? k_c_step<L, SP, BY, ZCH, MINB, true> : k_c_step<L, SP, BY, ZCH, MINB, false>;
+        kern<<<grid(ctx), dim3(32, BY), smem_c, ctx->stream>>>(
+            ctx->kp, (const S*)ctx->h[cur], (S*)ctx->h[nxt], (const R*)ctx->phi[cur], (const R*)ctx->phi[nxt],
             (const R*)ctx->c[cur], (R*)ctx->c[nxt]);
     }
     static void launch_init(lbpf_ctx* ctx) {
         const long long N = ctx->sp.N;
         k_init<L, SP><<<(unsigned)((N + 255) / 256), 256, 0, ctx->stream>>>(
-            ctx->sp, (const R*)ctx->phi[ctx->cur], (const R*)ctx->c[ctx->cur], (S*)ctx->g[ctx->cur],
+            ctx->kp, (const R*)ctx->phi[ctx->cur], (const R*)ctx->c[ctx->cur], (S*)ctx->g[ctx->cur],
             (S*)ctx->h[ctx->cur]);
     }
     static void launch_pops_out(lbpf_ctx* ctx, double* g, double* h) {
         const long long N = ctx->sp.N;
         const int cur = ctx->cur;
         k_pops_out<L, SP><<<(unsigned)((N + 255) / 256), 256, 0, ctx->stream>>>(
-            ctx->sp, (const R*)ctx->phi[cur], (const R*)ctx->c[cur], (const S*)ctx->g[cur],
+            ctx->kp, (const R*)ctx->phi[cur], (const R*)ctx->c[cur], (const S*)ctx->g[cur],
             (const S*)ctx->h[cur], g, h);
     }
     static const Dispatch* table() {
@@ -159,6 +194,7 @@ lbpf_status validate(const lbpf_params* p, std::string& why) {
     if (p->lattice != LBPF_D2Q9 && p->lattice != LBPF_D3Q19) return bad("unknown lattice");
     if (p->lattice == LBPF_D2Q9 && p->nz != 1) return bad("D2Q9 needs nz == 1");
     if ((long long)p->nx * p->ny * p->nz > (1LL << 40)) return bad("grid too large");
+    if ((long long)p->nx * p->ny >= (1LL << 31)) return bad("a z-plane must hold fewer than 2^31 nodes");
     for (int a = 0; a < 3; ++a) {
         if (p->bc[a] != LBPF_PERIODIC && p->bc[a] != LBPF_BOUNCEBACK) return bad("unknown boundary type");
         const int n = a == 0 ? p->nx : (a == 1 ? p->ny : p->nz);
@@ -243,7 +279,7 @@ template <typename R>
 void launch_fields_out(lbpf_ctx* ctx, double* ophi, double* oc, double* omu) {
     const long long N = ctx->sp.N;
     k_fields_out<R><<<(unsigned)((N + 255) / 256), 256, 0, ctx->stream>>>(
-        ctx->sp, (const R*)ctx->phi[ctx->cur], (const R*)ctx->c[ctx->cur], ophi, oc, omu);
+        ctx->kp, (const R*)ctx->phi[ctx->cur], (const R*)ctx->c[ctx->cur], ophi, oc, omu);
 }
 
 template <typename R>
@@ -292,6 +328,19 @@ lbpf_status lbpf_create(const lbpf_params* p, const double* phi0, const double* 
     ctx->p = *p;
     ctx->sp = lattice_units(p);
     ctx->q = p->lattice == LBPF_D3Q19 ? 19 : 9;
+    ctx->kp.P = ctx->sp;
+    ctx->kp.cd = make_coef<double>(ctx->sp);
+    ctx->kp.cf = make_coef<float>(ctx->sp);
+    for (int k = 0; k < 19; ++k) {
+        int e[3] = {0, 0, 0};
+        if (k < ctx->q) {
+            if (p->lattice == LBPF_D3Q19) { e[0] = D3Q19::ex(k); e[1] = D3Q19::ey(k); e[2] = D3Q19::ez(k); }
+            else { e[0] = D2Q9::ex(k); e[1] = D2Q9::ey(k); }
+        }
+        const long long nx = p->nx, nxy = (long long)p->nx * p->ny;
+        ctx->kp.kN[k] = (long long)k * ctx->sp.N;
+        ctx->kp.koff[k] = ctx->kp.kN[k] - (e[0] + e[1] * nx + e[2] * nxy);
+    }
     ctx->ops = ops;
     ctx->stream = (cudaStream_t)cuda_stream;
     ctx->real_size = p->precision == LBPF_FP64 ? 8 : 4;

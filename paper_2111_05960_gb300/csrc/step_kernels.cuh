@@ -52,6 +52,50 @@ struct StepParams {
     int counter_term;
 };
 
+// Derived constants of one simulation in the compute type, precomputed on the
+// host so that FP32 kernels carry no FP64 arithmetic:
+//   S_phi = kS phi (1 - phi)(mu - mu_eq),  kS = 6 (c_s^co - c_l^co)   (p' = 6 phi (1 - phi))
+//   G^st = kst S_phi,  kst = -lambda M / W^2;  G^dw = kdw omega',  kdw = -8 M / W^2
+//   counter-term magnitude (4/W) phi (1 - phi) = kct phi (1 - phi)
+//   j_at = atk dphi n,  atk = a W (c_s^co - c_l^co)
+template <typename R>
+struct Coef {
+    R mu_eq, c_l, c_s, kS, kst, kdw, kct, D_l, D_s, Dp, gamma, atk, omg, omh, eps2;
+};
+
+template <typename R>
+__host__ Coef<R> make_coef(const StepParams& P) {
+    Coef<R> c;
+    c.mu_eq = R(P.mu_eq); c.c_l = R(P.c_l); c.c_s = R(P.c_s);
+    c.kS = R(6.0 * (P.c_s - P.c_l));
+    c.kst = R(-P.lambda * P.M / (P.W * P.W));
+    c.kdw = R(P.counter_term ? 0.0 : -8.0 * P.M / (P.W * P.W));
+    c.kct = R(P.counter_term ? 4.0 / P.W : 0.0);
+    c.D_l = R(P.D_l); c.D_s = R(P.D_s); c.Dp = R(P.D_l - P.D_s);
+    c.gamma = R(P.gamma);
+    c.atk = R(P.a_at * P.W * (P.c_s - P.c_l));
+    c.omg = R(P.omg); c.omh = R(P.omh); c.eps2 = R(P.eps2);
+    return c;
+}
+
+// Everything a step kernel needs: geometry and the constants in both types.
+struct KParams {
+    StepParams P;
+    Coef<double> cd;
+    Coef<float> cf;
+    // per link k: k N - (ex + ey nx + ez nx ny), the element offset of the upstream
+    // population from x for a node whose neighbours are all inside (no wrap), and k N
+    long long koff[19];
+    long long kN[19];
+};
+
+template <typename R>
+__device__ __forceinline__ const Coef<R>& coef(const KParams& K);
+template <>
+__device__ __forceinline__ const Coef<double>& coef<double>(const KParams& K) { return K.cd; }
+template <>
+__device__ __forceinline__ const Coef<float>& coef<float>(const KParams& K) { return K.cf; }
+
 // ---- storage policies --------------------------------------------------------
 // A policy maps a population between its stored form and the compute type.
 // `ref` is the population's equilibrium value at the node it is stored at; the
@@ -103,6 +147,7 @@ struct StoreBF16Dev {
 // ---- helpers ------------------------------------------------------------------
 
 __device__ __forceinline__ int map_coord(int i, int n, int bc) {
+    if (i >= 0 && i < n) return i;
     if (bc == 0) {
         i %= n;
         return i < 0 ? i + n : i;
@@ -130,16 +175,118 @@ __device__ __forceinline__ R edot(int k, R vx, R vy, R vz) {
     return s;
 }
 
-// grad(phi) by directional derivatives (Eq. DerivDirec_Grad, Eq. Grad) from a
-// shared-memory tile; `c` is the node's offset in the tile, sx/sy the strides.
-template <class L, typename R>
-__device__ __forceinline__ void tile_gradient(const R* t, int c, int sx, int sy, R& gx, R& gy, R& gz) {
+template <typename R>
+__device__ __forceinline__ R rsqrt_reg(R g2, R eps2);
+template <>
+__device__ __forceinline__ double rsqrt_reg<double>(double g2, double eps2) { return 1.0 / sqrt(g2 + eps2); }
+template <>
+__device__ __forceinline__ float rsqrt_reg<float>(float g2, float eps2) { return 1.0f / sqrtf(g2 + eps2); }
+
+// G^st + G^dw: the isotropic part of G_k / w_k (Eq. SourceG_ST, Eq. SourceG_dw;
+// S_phi of Eq. SourceTerm_Coexistence with p' = 6 phi (1 - phi);
+// omega' = 2 phi (1 - phi)(1 - 2 phi) of Tab. 2).  kdw = 0 with the counter term.
+template <typename R>
+__device__ __forceinline__ R g_isotropic(const Coef<R>& C, R phi, R mu) {
+    const R pq = phi * (R(1) - phi);
+    const R S = C.kS * pq * (mu - C.mu_eq);
+    return C.kst * S + C.kdw * (R(2) * pq * (R(1) - R(2) * phi));
+}
+
+// Closure mu = mu_eq + c - c^co(phi) (Eq. PotChim_Equilibirum, h = phi).
+template <typename R>
+__device__ __forceinline__ R closure_mu(const Coef<R>& C, R phi, R c) {
+    return C.mu_eq + c - (C.c_l * phi + C.c_s * (R(1) - phi));
+}
+
+// P = gamma D(phi) mu with D = D_l phi + D_s (1 - phi) (Sec. 2.3.3).
+template <typename R>
+__device__ __forceinline__ R p_term(const Coef<R>& C, R phi, R mu) {
+    return C.gamma * (C.D_l * phi + C.D_s * (R(1) - phi)) * mu;
+}
+
+// ---- z-marching tile geometry ------------------------------------------------------
+// A block of 32 x BY threads owns an x-y tile and walks a chunk of ZCH planes
+// along z (2-D: one plane).  Shared memory holds rolling windows: phi^n for the
+// planes z-2..z+2 with a 2-node x-y halo, and the per-node ingredients for the
+// planes z-1..z+1 with a 1-node x-y ring.
+
+template <typename R>
+struct alignas(4 * sizeof(R)) V4 {
+    R a, b, c, d;
+};
+
+template <class L, int BY>
+struct Geo {
+    static constexpr int BX = 32;
+    static constexpr int X2 = BX + 4, Y2 = BY + 4;   // phi plane with a 2-node halo
+    static constexpr int X1 = BX + 2, Y1 = BY + 2;   // ingredient plane with a 1-node ring
+    static constexpr int P2 = X2 * Y2, P1 = X1 * Y1;
+    static constexpr int NPHI = (L::D == 3) ? 5 : 1; // phi planes in the window
+    static constexpr int NING = (L::D == 3) ? 3 : 1; // ingredient planes in the window
+    static constexpr int NT = BX * BY;
+};
+
+// Wrap (periodic) or mirror (wall) an index that is at most one node outside.
+__device__ __forceinline__ int wrap1(int i, int n, int bc) {
+    if (i < 0) return bc ? 0 : i + n;
+    if (i >= n) return bc ? n - 1 : i - n;
+    return i;
+}
+
+// Asynchronous global -> shared copies (cp.async, 4 or 8 bytes per element): the
+// next plane's inputs stream into shared memory while the current plane computes.
+template <typename R>
+__device__ __forceinline__ void cp_async(R* smem_dst, const R* gsrc) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    if (sizeof(R) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Start the copy of one phi plane (global z index zg, possibly outside) with its
+// 2-node halo (wrapped or mirrored).
+template <class L, int BY, typename R>
+__device__ __forceinline__ void async_phi_plane(const StepParams& P, const R* __restrict__ phi, R* dst,
+                                                int x0, int y0, int zg, bool inside2) {
+    using G = Geo<L, BY>;
+    const int tid = threadIdx.x + G::BX * threadIdx.y;
+    const int gz = (L::D == 3) ? map_coord(zg, P.nz, P.bc[2]) : 0;
+    const R* src = phi + (long long)gz * P.nx * P.ny;
+    constexpr int IT = (G::P2 + G::NT - 1) / G::NT;
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        const int s = tid + it * G::NT;
+        if (s < G::P2) {
+            const int ly = s / G::X2, lx = s - ly * G::X2;
+            int gx = x0 + lx - 2, gy = y0 + ly - 2;
+            if (!inside2) {
+                gx = map_coord(gx, P.nx, P.bc[0]);
+                gy = map_coord(gy, P.ny, P.bc[1]);
+            }
+            cp_async(dst + s, src + (long long)gy * P.nx + gx);
+        }
+    }
+}
+
+// grad(phi) by directional derivatives (Eq. DerivDirec_Grad, Eq. Grad) at offset c
+// of the plane p0, with pm / pp the planes below / above.  Opposite links give
+// the same term, so each pair is counted once, doubled.
+template <class L, int BY, typename R>
+__device__ __forceinline__ void plane_gradient(const R* pm, const R* p0, const R* pp, int c,
+                                               R& gx, R& gy, R& gz) {
+    using G = Geo<L, BY>;
     gx = gy = gz = R(0);
 #pragma unroll
     for (int k = 1; k < L::Q; ++k) {
-        const int off = L::ex(k) + L::ey(k) * sx + L::ez(k) * sy;
-        const R dk = R(0.5) * (t[c + off] - t[c - off]);
-        const R cw = R(3.0 * L::w(k));
+        if (L::opp(k) < k) continue;   // one link of each opposite pair
+        const int off = L::ex(k) + G::X2 * L::ey(k);
+        const R* fwd = L::ez(k) > 0 ? pp : (L::ez(k) < 0 ? pm : p0);
+        const R* bwd = L::ez(k) > 0 ? pm : (L::ez(k) < 0 ? pp : p0);
+        const R dk = fwd[c + off] - bwd[c - off];
+        const R cw = R(3.0 * L::w(k));        // 2 (pair) x 3 w_k x 1/2 (central difference)
         if (L::ex(k) > 0) gx += cw * dk;
         if (L::ex(k) < 0) gx -= cw * dk;
         if (L::ey(k) > 0) gy += cw * dk;
@@ -151,282 +298,365 @@ __device__ __forceinline__ void tile_gradient(const R* t, int c, int sx, int sy,
     }
 }
 
-template <typename R>
-__device__ __forceinline__ R rsqrt_reg(R g2, R eps2);
-template <>
-__device__ __forceinline__ double rsqrt_reg<double>(double g2, double eps2) { return 1.0 / sqrt(g2 + eps2); }
-template <>
-__device__ __forceinline__ float rsqrt_reg<float>(float g2, float eps2) { return 1.0f / sqrtf(g2 + eps2); }
-
-// G^st + G^dw: the isotropic part of G_k / w_k (Eq. SourceG_ST, Eq. SourceG_dw;
-// S_phi of Eq. SourceTerm_Coexistence with p' = 6 phi (1 - phi)).
-template <typename R>
-__device__ __forceinline__ R g_isotropic(const StepParams& P, R phi, R mu) {
-    const R one = R(1);
-    const R S = R(6) * phi * (one - phi) * R(P.c_s - P.c_l) * (mu - R(P.mu_eq));
-    R A = -R(P.lambda) * R(P.M) * S / (R(P.W) * R(P.W));
-    if (!P.counter_term) {
-        const R wp = R(2) * phi * (one - phi) * (one - R(2) * phi);
-        A -= (R(8) * R(P.M) / (R(P.W) * R(P.W))) * wp;
+// Linear index of the ring node (lx, ly) of plane zg (1-node ring, maybe outside).
+template <class L, int BY>
+__device__ __forceinline__ long long ring_index(const StepParams& P, int x0, int y0, int lx, int ly, int gz,
+                                                bool inside1) {
+    int gx = x0 + lx - 1, gy = y0 + ly - 1;
+    if (!inside1) {
+        gx = wrap1(gx, P.nx, P.bc[0]);
+        gy = wrap1(gy, P.ny, P.bc[1]);
     }
-    return A;
+    return ((long long)gz * P.ny + gy) * P.nx + gx;
 }
 
-template <typename R>
-__device__ __forceinline__ R closure_mu(const StepParams& P, R phi, R c) {
-    return R(P.mu_eq) + c - (R(P.c_l) * phi + R(P.c_s) * (R(1) - phi));
-}
-
-// P = gamma D(phi) mu with D = D_l phi + D_s (1 - phi) (Sec. 2.3.3).
-template <typename R>
-__device__ __forceinline__ R p_term(const StepParams& P, R phi, R mu) {
-    const R D = R(P.D_l) * phi + R(P.D_s) * (R(1) - phi);
-    return R(P.gamma) * D * mu;
-}
-
-// ---- tile geometry -------------------------------------------------------------
-
-template <class L, int BY, int BZ>
-struct Tile {
-    static constexpr int BX = 32;
-    static constexpr int RZ = (L::D == 3) ? 1 : 0;
-    static constexpr int X2 = BX + 4, Y2 = BY + 4, Z2 = BZ + 4 * RZ;   // phi halo 2
-    static constexpr int X1 = BX + 2, Y1 = BY + 2, Z1 = BZ + 2 * RZ;   // ingredient ring 1
-    static constexpr int N2 = X2 * Y2 * Z2;
-    static constexpr int N1 = X1 * Y1 * Z1;
-    static constexpr int NT = BX * BY * BZ;
-};
-
-// Load phi of the tile plus a 2-node halo (wrapped or mirrored).
-template <class L, int BY, int BZ, typename R>
-__device__ __forceinline__ void load_phi_halo(const StepParams& P, const R* __restrict__ phi, R* s,
-                                              int x0, int y0, int z0) {
-    using T = Tile<L, BY, BZ>;
-    const int tid = threadIdx.x + T::BX * (threadIdx.y + BY * threadIdx.z);
-    for (int s_i = tid; s_i < T::N2; s_i += T::NT) {
-        const int lx = s_i % T::X2;
-        const int ly = (s_i / T::X2) % T::Y2;
-        const int lz = s_i / (T::X2 * T::Y2);
-        const int gx = map_coord(x0 + lx - 2, P.nx, P.bc[0]);
-        const int gy = map_coord(y0 + ly - 2, P.ny, P.bc[1]);
-        const int gz = (L::D == 3) ? map_coord(z0 + lz - 2, P.nz, P.bc[2]) : 0;
-        s[s_i] = phi[((long long)gz * P.ny + gy) * P.nx + gx];
-    }
-}
-
-// ---- phi kernel ------------------------------------------------------------------
-
-template <class L, class SP, int BY, int BZ>
-__global__ void __launch_bounds__(32 * BY * BZ)
-k_phi_step(const StepParams P, const typename SP::store_t* __restrict__ gin,
-           typename SP::store_t* __restrict__ gout, const typename SP::real* __restrict__ phi_n,
-           const typename SP::real* __restrict__ c_n, typename SP::real* __restrict__ phi_np1) {
-    using R = typename SP::real;
-    using T = Tile<L, BY, BZ>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    R* sphi = reinterpret_cast<R*>(smem_raw);
-    R* s_alpha = sphi + T::N2;           // alpha_g
-    R* s_bx = s_alpha + T::N1;           // beta_g
-    R* s_by = s_bx + T::N1;
-    R* s_bz = s_by + T::N1;              // (3-D only)
-    R* s_A = s_bz + (L::D == 3 ? T::N1 : 0);  // G^st + G^dw, for the phi moment
-
-    const int x0 = blockIdx.x * T::BX, y0 = blockIdx.y * BY, z0 = blockIdx.z * BZ;
-    const int tid = threadIdx.x + T::BX * (threadIdx.y + BY * threadIdx.z);
-    const R omg = R(P.omg);
-    const R half_src = R(1) - R(0.5) * omg;
-
-    load_phi_halo<L, BY, BZ>(P, phi_n, sphi, x0, y0, z0);
-    __syncthreads();
-
-    // ingredients on the tile plus a 1-node ring
-    for (int s_i = tid; s_i < T::N1; s_i += T::NT) {
-        const int lx = s_i % T::X1;
-        const int ly = (s_i / T::X1) % T::Y1;
-        const int lz = s_i / (T::X1 * T::Y1);
-        const int c2 = (lx + 1) + T::X2 * ((ly + 1) + T::Y2 * (lz + T::RZ));
-        const int gx = map_coord(x0 + lx - 1, P.nx, P.bc[0]);
-        const int gy = map_coord(y0 + ly - 1, P.ny, P.bc[1]);
-        const int gz = (L::D == 3) ? map_coord(z0 + lz - 1, P.nz, P.bc[2]) : 0;
-        const R ph = sphi[c2];
-        const R c = c_n[((long long)gz * P.ny + gy) * P.nx + gx];
-        const R mu = closure_mu(P, ph, c);
-        const R A = g_isotropic(P, ph, mu);
-        s_A[s_i] = A;
-        s_alpha[s_i] = omg * ph + half_src * A;
-        if (P.counter_term) {
-            R gx_, gy_, gz_;
-            tile_gradient<L>(sphi, c2, T::X2, T::X2 * T::Y2, gx_, gy_, gz_);
-            const R inv = rsqrt_reg<R>(gx_ * gx_ + gy_ * gy_ + gz_ * gz_, R(P.eps2));
-            const R kct = half_src * (R(4) / R(P.W)) * ph * (R(1) - ph) * inv;  // (4/W) phi(1-phi) n
-            s_bx[s_i] = kct * gx_;
-            s_by[s_i] = kct * gy_;
-            if (L::D == 3) s_bz[s_i] = kct * gz_;
-        } else {
-            s_bx[s_i] = R(0);
-            s_by[s_i] = R(0);
-            if (L::D == 3) s_bz[s_i] = R(0);
+// Start the copy of a field on the 1-node ring of plane zg into shared memory.
+template <class L, int BY, typename R>
+__device__ __forceinline__ void async_ring(const StepParams& P, const R* __restrict__ f, R* dst, int x0, int y0,
+                                           int zg, bool inside1) {
+    using G = Geo<L, BY>;
+    const int tid = threadIdx.x + G::BX * threadIdx.y;
+    const int gz = (L::D == 3) ? map_coord(zg, P.nz, P.bc[2]) : 0;
+    constexpr int IT = (G::P1 + G::NT - 1) / G::NT;
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        const int s = tid + it * G::NT;
+        if (s < G::P1) {
+            const int ly = s / G::X1, lx = s - ly * G::X1;
+            cp_async(dst + s, f + ring_index<L, BY>(P, x0, y0, lx, ly, gz, inside1));
         }
     }
-    __syncthreads();
+}
 
-    const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
-    const int x = x0 + tx, y = y0 + ty, z = z0 + tz;
-    if (x >= P.nx || y >= P.ny || z >= P.nz) return;
-    const long long N = P.N;
-    const long long xi = ((long long)z * P.ny + y) * P.nx + x;
-    const int c1 = (tx + 1) + T::X1 * ((ty + 1) + T::Y1 * (tz + T::RZ));
-    const int c2 = (tx + 2) + T::X2 * ((ty + 2) + T::Y2 * (tz + 2 * T::RZ));
+// Ingredients of the phi collision on one plane: alpha_g, beta_g (x, y, z) and
+// A = G^st + G^dw.
+template <class L, int BY, typename R>
+__device__ __forceinline__ void phi_ingredients(const StepParams& P, const Coef<R>& C, const R* cst,
+                                                const R* pm, const R* p0, const R* pp, V4<R>* ing, R* sA) {
+    using G = Geo<L, BY>;
+    const int tid = threadIdx.x + G::BX * threadIdx.y;
+    const R half_src = R(1) - R(0.5) * C.omg;
+    constexpr int IT = (G::P1 + G::NT - 1) / G::NT;
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        const int s = tid + it * G::NT;
+        if (s >= G::P1) break;
+        const int ly = s / G::X1, lx = s - ly * G::X1;
+        const int c2 = (ly + 1) * G::X2 + (lx + 1);
+        const R ph = p0[c2];
+        const R mu = closure_mu(C, ph, cst[s]);
+        const R A = g_isotropic(C, ph, mu);
+        V4<R> v;
+        v.a = C.omg * ph + half_src * A;
+        if (P.counter_term) {
+            R gx, gy, gz_;
+            plane_gradient<L, BY>(pm, p0, pp, c2, gx, gy, gz_);
+            const R inv = rsqrt_reg<R>(gx * gx + gy * gy + gz_ * gz_, C.eps2);
+            const R k = half_src * C.kct * ph * (R(1) - ph) * inv;   // (4/W) phi (1 - phi) n
+            v.b = k * gx; v.c = k * gy; v.d = k * gz_;
+        } else {
+            v.b = v.c = v.d = R(0);
+        }
+        ing[s] = v;
+        sA[s] = A;
+    }
+}
+
+// Ingredients of the h collision on one plane: P = gamma D mu and
+// beta_h = (1 - w_h/2) gamma (mu D' grad phi + j_at).
+template <class L, int BY, typename R>
+__device__ __forceinline__ void c_ingredients(const StepParams& P, const Coef<R>& C, const R* cst, const R* pst,
+                                              const R* pm, const R* p0, const R* pp, V4<R>* ing) {
+    using G = Geo<L, BY>;
+    const int tid = threadIdx.x + G::BX * threadIdx.y;
+    const R kk = (R(1) - R(0.5) * C.omh) * C.gamma;
+    constexpr int IT = (G::P1 + G::NT - 1) / G::NT;
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        const int s = tid + it * G::NT;
+        if (s >= G::P1) break;
+        const int ly = s / G::X1, lx = s - ly * G::X1;
+        const int c2 = (ly + 1) * G::X2 + (lx + 1);
+        const R ph = p0[c2];
+        const R dphi = pst[s] - ph;                        // explicit Euler dphi/dt
+        const R mu = closure_mu(C, ph, cst[s]);
+        R gx, gy, gz_;
+        plane_gradient<L, BY>(pm, p0, pp, c2, gx, gy, gz_);
+        const R inv = rsqrt_reg<R>(gx * gx + gy * gy + gz_ * gz_, C.eps2);
+        const R f = mu * C.Dp + C.atk * dphi * inv;        // F = (mu D' + j_at / |grad|) grad
+        V4<R> v;
+        v.a = p_term(C, ph, mu);
+        v.b = kk * f * gx; v.c = kk * f * gy; v.d = kk * f * gz_;
+        ing[s] = v;
+    }
+}
+
+// Pull of one plane, in two stages so that the population loads of plane z are
+// in flight while the block computes the ingredients of plane z+1.
+//
+// Upstream node of link k: (x - ex, y - ey, z - ez), wrapped on periodic axes;
+// beyond a wall the link bounces back to the node itself.  `fast`: every
+// upstream node is inside, so the source is xi + koff[k] (one add).  Otherwise
+// the wrapped x index, row and plane offsets for e = -1, 0, 1 are computed once
+// and a link's source costs two adds and no branch.
+template <class L, class SP, bool IS_PHI, bool WALLS>
+struct PullState {
+    using R = typename SP::real;
+    R old[L::Q];
+    R cx;
+    unsigned wallmask;
+    long long xi;
+};
+
+template <class L, class SP, bool IS_PHI, bool WALLS>
+__device__ __forceinline__ void pull_load(const KParams& K, const typename SP::store_t* __restrict__ fin,
+                                          const typename SP::real* __restrict__ c_n, int x, int y, int z, bool fast,
+                                          PullState<L, SP, IS_PHI, WALLS>& st) {
+    using R = typename SP::real;
+    const StepParams& P = K.P;
+    const long long nxy = (long long)P.nx * P.ny;
+    const long long xi = (long long)z * nxy + (long long)y * P.nx + x;
+    st.xi = xi;
+    st.wallmask = 0u;
+    st.cx = IS_PHI ? R(0) : c_n[xi];
+    if (fast) {
+        const typename SP::store_t* base = fin + xi;
+#pragma unroll
+        for (int k = 0; k < L::Q; ++k) st.old[k] = SP::load(base, K.koff[k], R(0));
+        return;
+    }
+    // source offsets indexed by e + 1: e = +1 reads the node at -1, e = -1 the node at +1
+    int SX[3], SY[3];
+    long long SZ[3];
+    bool WX[3], WY[3], WZ[3];
+    {
+        const bool lo = x == 0, hi = x == P.nx - 1;
+        SX[1] = x; WX[1] = false;
+        SX[2] = lo ? (WALLS && P.bc[0] ? x : P.nx - 1) : x - 1; WX[2] = WALLS && lo && P.bc[0];
+        SX[0] = hi ? (WALLS && P.bc[0] ? x : 0) : x + 1;        WX[0] = WALLS && hi && P.bc[0];
+    }
+    {
+        const bool lo = y == 0, hi = y == P.ny - 1;
+        SY[1] = y * P.nx; WY[1] = false;
+        SY[2] = (lo ? (WALLS && P.bc[1] ? y : P.ny - 1) : y - 1) * P.nx; WY[2] = WALLS && lo && P.bc[1];
+        SY[0] = (hi ? (WALLS && P.bc[1] ? y : 0) : y + 1) * P.nx;        WY[0] = WALLS && hi && P.bc[1];
+    }
+    if (L::D == 3) {
+        const bool lo = z == 0, hi = z == P.nz - 1;
+        SZ[1] = z * nxy; WZ[1] = false;
+        SZ[2] = (long long)(lo ? (WALLS && P.bc[2] ? z : P.nz - 1) : z - 1) * nxy; WZ[2] = WALLS && lo && P.bc[2];
+        SZ[0] = (long long)(hi ? (WALLS && P.bc[2] ? z : 0) : z + 1) * nxy;        WZ[0] = WALLS && hi && P.bc[2];
+    } else {
+        SZ[0] = SZ[1] = SZ[2] = 0; WZ[0] = WZ[1] = WZ[2] = false;
+    }
+#pragma unroll
+    for (int k = 0; k < L::Q; ++k) {
+        const bool wall = WALLS && (WX[L::ex(k) + 1] || WY[L::ey(k) + 1] || WZ[L::ez(k) + 1]);
+        const long long si = SZ[L::ez(k) + 1] + SY[L::ey(k) + 1] + SX[L::ex(k) + 1];
+        // half-way bounce-back: f_k(x, n+1) = f*_{opp k}(x, n)
+        const long long addr = wall ? K.kN[L::opp(k)] + xi : K.kN[k] + si;
+        st.old[k] = SP::load(fin, addr, R(0));
+        st.wallmask |= (wall ? 1u : 0u) << k;
+    }
+}
+
+// Collision of each pulled population at its upstream node from the ingredient
+// planes im (z-1), i0 (z), ip (z+1) (phi planes fm, f0, fp likewise), the new
+// moment, and the stores.
+template <class L, class SP, int BY, bool IS_PHI, bool WALLS>
+__device__ __forceinline__ void pull_combine(const KParams& K, const Coef<typename SP::real>& C,
+                                             typename SP::store_t* __restrict__ fout,
+                                             const V4<typename SP::real>* im, const V4<typename SP::real>* i0,
+                                             const V4<typename SP::real>* ip, const typename SP::real* fm,
+                                             const typename SP::real* f0, const typename SP::real* fp,
+                                             const typename SP::real* sA,
+                                             const typename SP::real* __restrict__ phi_np1_in,
+                                             typename SP::real* __restrict__ moment_out,
+                                             const PullState<L, SP, IS_PHI, WALLS>& st) {
+    using R = typename SP::real;
+    using G = Geo<L, BY>;
+    const long long xi = st.xi;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int c1 = (ty + 1) * G::X1 + (tx + 1);
+    const int c2 = (ty + 2) * G::X2 + (tx + 2);
+    const R om = IS_PHI ? C.omg : C.omh;
+    const R keep = R(1) - om;
+    // without deviation storage a population is stored as soon as it is known
+    constexpr bool hold = SP::deviation;
+    typename SP::store_t* out = fout + xi;
 
     R v[L::Q];
     R sum = R(0);
+    constexpr int k0 = IS_PHI ? 0 : 1;
+    if (!IS_PHI) {
+        // rest population of h: h*_0 = (1 - w_h) h_0 + w_h h^eq_0 (H_0 = 0)
+        const R heq0 = st.cx - (R(1) - R(L::w(0))) * i0[c1].a;
+        v[0] = keep * (SP::deviation ? st.old[0] + heq0 : st.old[0]) + om * heq0;
+        sum = v[0];
+        if (!hold) SP::store(out, K.kN[0], v[0], R(0));
+    }
 #pragma unroll
-    for (int k = 0; k < L::Q; ++k) {
-        const int ux = x - L::ex(k), uy = y - L::ey(k), uz = z - L::ez(k);
-        bool wall = false;
-        if (L::ex(k) != 0 && P.bc[0] && (ux < 0 || ux >= P.nx)) wall = true;
-        if (L::ey(k) != 0 && P.bc[1] && (uy < 0 || uy >= P.ny)) wall = true;
-        if (L::D == 3 && L::ez(k) != 0 && P.bc[2] && (uz < 0 || uz >= P.nz)) wall = true;
-        R val;
-        if (wall) {
-            // half-way bounce-back: g_k(x, n+1) = g*_{opp k}(x, n)
-            const int ko = L::opp(k);
-            const R wk = R(L::w(k));
-            const R gold = SP::load(gin, (long long)ko * N + xi, wk * sphi[c2]);
-            const R bz = (L::D == 3) ? s_bz[c1] : R(0);
-            val = (R(1) - omg) * gold + wk * (s_alpha[c1] - edot<L>(k, s_bx[c1], s_by[c1], bz));
-        } else {
-            const int sx = map_coord(ux, P.nx, P.bc[0]);
-            const int sy = map_coord(uy, P.ny, P.bc[1]);
-            const int sz = (L::D == 3) ? map_coord(uz, P.nz, P.bc[2]) : 0;
-            const long long si = ((long long)sz * P.ny + sy) * P.nx + sx;
-            const int o1 = c1 - (L::ex(k) + T::X1 * (L::ey(k) + T::Y1 * L::ez(k)));
-            const int o2 = c2 - (L::ex(k) + T::X2 * (L::ey(k) + T::Y2 * L::ez(k)));
-            const R wk = R(L::w(k));
-            const R gold = SP::load(gin, (long long)k * N + si, wk * sphi[o2]);
-            const R bz = (L::D == 3) ? s_bz[o1] : R(0);
-            val = (R(1) - omg) * gold + wk * (s_alpha[o1] + edot<L>(k, s_bx[o1], s_by[o1], bz));
+    for (int k = k0; k < L::Q; ++k) {
+        const R wk = R(L::w(k));
+        const bool wall = WALLS && ((st.wallmask >> k) & 1u);
+        const V4<R>* ik = L::ez(k) > 0 ? im : (L::ez(k) < 0 ? ip : i0);   // upstream plane z - ez
+        const R* fk = L::ez(k) > 0 ? fm : (L::ez(k) < 0 ? fp : f0);
+        const V4<R> g = wall ? i0[c1] : ik[c1 - L::ex(k) - G::X1 * L::ey(k)];
+        const R sgn = wall ? R(-1) : R(1);
+        R f_old = st.old[k];
+        if (SP::deviation) {
+            const R ref = IS_PHI ? wk * (wall ? f0[c2] : fk[c2 - L::ex(k) - G::X2 * L::ey(k)]) : wk * g.a;
+            f_old += ref;
         }
+        const R a = IS_PHI ? g.a : om * g.a;
+        const R val = keep * f_old + wk * (a + sgn * edot<L>(k, g.b, g.c, g.d));
         v[k] = val;
         sum += val;
+        if (!hold) SP::store(out, K.kN[k], val, R(0));
     }
-    const R phin = sum + R(0.5) * s_A[c1];
-    phi_np1[xi] = phin;
+    if (IS_PHI) {
+        const R phin = sum + R(0.5) * sA[c1];     // Eq. Moment_Phi
+        moment_out[xi] = phin;
+        if (hold) {
 #pragma unroll
-    for (int k = 0; k < L::Q; ++k) SP::store(gout, (long long)k * N + xi, v[k], R(L::w(k)) * phin);
+            for (int k = 0; k < L::Q; ++k) SP::store(out, K.kN[k], v[k], R(L::w(k)) * phin);
+        }
+    } else {
+        moment_out[xi] = sum;                      // Eq. Moment0_LBM_Concent
+        if (hold) {
+            const R phin = phi_np1_in[xi];
+            const R Pn = p_term(C, phin, closure_mu(C, phin, sum));
+            SP::store(out, K.kN[0], v[0], sum - (R(1) - R(L::w(0))) * Pn);
+#pragma unroll
+            for (int k = 1; k < L::Q; ++k) SP::store(out, K.kN[k], v[k], R(L::w(k)) * Pn);
+        }
+    }
 }
 
-// ---- composition kernel -------------------------------------------------------------
+// One z-marching pass of either kernel.
+template <class L, class SP, int BY, int ZCH, bool IS_PHI, bool WALLS>
+__device__ __forceinline__ void march(const KParams& K, const typename SP::store_t* __restrict__ fin,
+                                      typename SP::store_t* __restrict__ fout,
+                                      const typename SP::real* __restrict__ phi_n,
+                                      const typename SP::real* __restrict__ phi_np1,
+                                      const typename SP::real* __restrict__ c_n,
+                                      typename SP::real* __restrict__ moment_out) {
+    using R = typename SP::real;
+    using G = Geo<L, BY>;
+    const StepParams& P = K.P;
+    const Coef<R>& C = coef<R>(K);
+    extern __shared__ __align__(32) unsigned char smem_raw[];
+    V4<R>* sing = reinterpret_cast<V4<R>*>(smem_raw);                 // [NING][P1]
+    R* sphi = reinterpret_cast<R*>(sing + G::NING * G::P1);          // [NPHI][P2]
+    R* cst = sphi + G::NPHI * G::P2;                                 // [2][P1] c^n on the ring
+    R* pst = cst + 2 * G::P1;                                        // [2][P1] phi^{n+1} (c kernel)
+    R* sA = pst + (IS_PHI ? 0 : 2 * G::P1);                          // [NING][P1] (phi kernel)
 
-template <class L, class SP, int BY, int BZ>
-__global__ void __launch_bounds__(32 * BY * BZ)
-k_c_step(const StepParams P, const typename SP::store_t* __restrict__ hin,
+    const int x0 = blockIdx.x * G::BX, y0 = blockIdx.y * BY;
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    const bool active_xy = x < P.nx && y < P.ny;
+    const bool inside2 = x0 >= 2 && x0 + G::BX + 2 <= P.nx && y0 >= 2 && y0 + BY + 2 <= P.ny;
+    const bool inside1 = x0 >= 1 && x0 + G::BX + 1 <= P.nx && y0 >= 1 && y0 + BY + 1 <= P.ny;
+    PullState<L, SP, IS_PHI, WALLS> st;
+
+    // the ring inputs of plane zg go to stage buffer zg & 1
+    auto fetch_ring = [&](int zg) {
+        const int b = zg & 1;
+        async_ring<L, BY>(P, c_n, cst + b * G::P1, x0, y0, zg, inside1);
+        if (!IS_PHI) async_ring<L, BY>(P, phi_np1, pst + b * G::P1, x0, y0, zg, inside1);
+    };
+    auto ingredients = [&](int slot_i, const R* pm, const R* p0, const R* pp, int zg) {
+        const int b = zg & 1;
+        if (IS_PHI)
+            phi_ingredients<L, BY>(P, C, cst + b * G::P1, pm, p0, pp, sing + slot_i * G::P1, sA + slot_i * G::P1);
+        else
+            c_ingredients<L, BY>(P, C, cst + b * G::P1, pst + b * G::P1, pm, p0, pp, sing + slot_i * G::P1);
+    };
+
+    if (L::D == 2) {
+        async_phi_plane<L, BY>(P, phi_n, sphi, x0, y0, 0, inside2);
+        fetch_ring(0);
+        cp_async_commit();
+        if (active_xy) pull_load<L, SP, IS_PHI, WALLS>(K, fin, c_n, x, y, 0, inside1, st);
+        cp_async_wait_all();
+        __syncthreads();
+        ingredients(0, sphi, sphi, sphi, 0);
+        __syncthreads();
+        if (active_xy)
+            pull_combine<L, SP, BY, IS_PHI, WALLS>(K, C, fout, sing, sing, sing, sphi, sphi, sphi, sA, phi_np1,
+                                                   moment_out, st);
+        return;
+    }
+
+    // z-march.  While plane z is pulled, the phi plane z+3 and the ring of z+2
+    // stream into shared memory, and the loads of plane z overlap the
+    // ingredients of z+1.  Stage buffers are indexed by zg & 1 (zg >= -1).
+    const int z0 = blockIdx.z * ZCH;
+    const int z1 = min(z0 + ZCH, P.nz);
+    auto fslot = [&](int zg) { return sphi + ((zg - z0 + 2 + 5 * ZCH) % 5) * G::P2; };
+    auto islot = [&](int zg) { return (zg - z0 + 1 + 3 * ZCH) % 3; };
+
+    for (int zg = z0 - 2; zg <= z0 + 1; ++zg) async_phi_plane<L, BY>(P, phi_n, fslot(zg), x0, y0, zg, inside2);
+    fetch_ring(z0 - 1);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    ingredients(islot(z0 - 1), fslot(z0 - 2), fslot(z0 - 1), fslot(z0), z0 - 1);
+    __syncthreads();                     // stage (z0 - 1) & 1 is reused by plane z0 + 1
+    fetch_ring(z0);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    ingredients(islot(z0), fslot(z0 - 1), fslot(z0), fslot(z0 + 1), z0);
+    async_phi_plane<L, BY>(P, phi_n, fslot(z0 + 2), x0, y0, z0 + 2, inside2);
+    fetch_ring(z0 + 1);
+    cp_async_commit();
+    for (int z = z0; z < z1; ++z) {
+        cp_async_wait_all();             // phi plane z+2 and the ring of z+1 have landed
+        __syncthreads();                 // ... for every thread; pull(z-1) is done everywhere
+        if (z + 1 < z1) {
+            // prefetch for the next plane: phi plane z+3 into the slot of z-2, ring of z+2
+            async_phi_plane<L, BY>(P, phi_n, fslot(z + 3), x0, y0, z + 3, inside2);
+            fetch_ring(z + 2);
+        }
+        cp_async_commit();
+        if (active_xy) pull_load<L, SP, IS_PHI, WALLS>(K, fin, c_n, x, y, z, inside1 && z >= 1 && z + 1 < P.nz, st);
+        ingredients(islot(z + 1), fslot(z), fslot(z + 1), fslot(z + 2), z + 1);
+        __syncthreads();
+        if (active_xy)
+            pull_combine<L, SP, BY, IS_PHI, WALLS>(K, C, fout, sing + islot(z - 1) * G::P1,
+                                                   sing + islot(z) * G::P1, sing + islot(z + 1) * G::P1,
+                                                   fslot(z - 1), fslot(z), fslot(z + 1), sA + islot(z) * G::P1,
+                                                   phi_np1, moment_out, st);
+    }
+    cp_async_wait_all();
+}
+
+template <class L, class SP, int BY, int ZCH>
+constexpr size_t march_smem(bool is_phi) {
+    using G = Geo<L, BY>;
+    using R = typename SP::real;
+    return sizeof(V4<R>) * G::NING * G::P1 + sizeof(R) * G::NPHI * G::P2 + sizeof(R) * 2 * G::P1 +
+           (is_phi ? sizeof(R) * G::NING * G::P1 : sizeof(R) * 2 * G::P1);
+}
+
+// ---- the two step kernels ----------------------------------------------------------
+
+template <class L, class SP, int BY, int ZCH, int MINB, bool WALLS>
+__global__ void __launch_bounds__(32 * BY, MINB)
+k_phi_step(const KParams K, const typename SP::store_t* __restrict__ gin,
+           typename SP::store_t* __restrict__ gout, const typename SP::real* __restrict__ phi_n,
+           const typename SP::real* __restrict__ c_n, typename SP::real* __restrict__ phi_np1) {
+    march<L, SP, BY, ZCH, true, WALLS>(K, gin, gout, phi_n, nullptr, c_n, phi_np1);
+}
+
+template <class L, class SP, int BY, int ZCH, int MINB, bool WALLS>
+__global__ void __launch_bounds__(32 * BY, MINB)
+k_c_step(const KParams K, const typename SP::store_t* __restrict__ hin,
          typename SP::store_t* __restrict__ hout, const typename SP::real* __restrict__ phi_n,
          const typename SP::real* __restrict__ phi_np1, const typename SP::real* __restrict__ c_n,
          typename SP::real* __restrict__ c_np1) {
-    using R = typename SP::real;
-    using T = Tile<L, BY, BZ>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    R* sphi = reinterpret_cast<R*>(smem_raw);
-    R* s_P = sphi + T::N2;               // gamma D mu
-    R* s_bx = s_P + T::N1;               // beta_h = (1 - w_h/2) gamma F
-    R* s_by = s_bx + T::N1;
-    R* s_bz = s_by + T::N1;
-
-    const int x0 = blockIdx.x * T::BX, y0 = blockIdx.y * BY, z0 = blockIdx.z * BZ;
-    const int tid = threadIdx.x + T::BX * (threadIdx.y + BY * threadIdx.z);
-    const R omh = R(P.omh);
-    const R half_src = R(1) - R(0.5) * omh;
-    const R Dp = R(P.D_l - P.D_s);
-    const R atk = R(P.a_at * P.W * (P.c_s - P.c_l));   // a W (c_s^co - c_l^co), 0 if off
-
-    load_phi_halo<L, BY, BZ>(P, phi_n, sphi, x0, y0, z0);
-    __syncthreads();
-
-    for (int s_i = tid; s_i < T::N1; s_i += T::NT) {
-        const int lx = s_i % T::X1;
-        const int ly = (s_i / T::X1) % T::Y1;
-        const int lz = s_i / (T::X1 * T::Y1);
-        const int c2 = (lx + 1) + T::X2 * ((ly + 1) + T::Y2 * (lz + T::RZ));
-        const int gx = map_coord(x0 + lx - 1, P.nx, P.bc[0]);
-        const int gy = map_coord(y0 + ly - 1, P.ny, P.bc[1]);
-        const int gz = (L::D == 3) ? map_coord(z0 + lz - 1, P.nz, P.bc[2]) : 0;
-        const long long gi = ((long long)gz * P.ny + gy) * P.nx + gx;
-        const R ph = sphi[c2];
-        const R c = c_n[gi];
-        const R mu = closure_mu(P, ph, c);
-        s_P[s_i] = p_term(P, ph, mu);
-        R gx_, gy_, gz_;
-        tile_gradient<L>(sphi, c2, T::X2, T::X2 * T::Y2, gx_, gy_, gz_);
-        const R inv = rsqrt_reg<R>(gx_ * gx_ + gy_ * gy_ + gz_ * gz_, R(P.eps2));
-        const R dphi = phi_np1[gi] - ph;                  // explicit Euler dphi/dt
-        const R jat = atk * dphi * inv;                   // j_at = a W dc dphi n
-        const R f = mu * Dp;
-        const R kk = half_src * R(P.gamma);
-        s_bx[s_i] = kk * (f * gx_ + jat * gx_);
-        s_by[s_i] = kk * (f * gy_ + jat * gy_);
-        if (L::D == 3) s_bz[s_i] = kk * (f * gz_ + jat * gz_);
-    }
-    __syncthreads();
-
-    const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
-    const int x = x0 + tx, y = y0 + ty, z = z0 + tz;
-    if (x >= P.nx || y >= P.ny || z >= P.nz) return;
-    const long long N = P.N;
-    const long long xi = ((long long)z * P.ny + y) * P.nx + x;
-    const int c1 = (tx + 1) + T::X1 * ((ty + 1) + T::Y1 * (tz + T::RZ));
-    const R w0 = R(L::w(0));
-    const R cx = c_n[xi];
-
-    R v[L::Q];
-    // rest population: h*_0 = (1 - w_h) h_0 + w_h h^eq_0, H_0 = 0
-    {
-        const R Px = s_P[c1];
-        const R heq0 = cx - (R(1) - w0) * Px;
-        const R h0 = SP::load(hin, xi, heq0);
-        v[0] = (R(1) - omh) * h0 + omh * heq0;
-    }
-    R sum = v[0];
-#pragma unroll
-    for (int k = 1; k < L::Q; ++k) {
-        const int ux = x - L::ex(k), uy = y - L::ey(k), uz = z - L::ez(k);
-        bool wall = false;
-        if (L::ex(k) != 0 && P.bc[0] && (ux < 0 || ux >= P.nx)) wall = true;
-        if (L::ey(k) != 0 && P.bc[1] && (uy < 0 || uy >= P.ny)) wall = true;
-        if (L::D == 3 && L::ez(k) != 0 && P.bc[2] && (uz < 0 || uz >= P.nz)) wall = true;
-        const R wk = R(L::w(k));
-        R val;
-        if (wall) {
-            const int ko = L::opp(k);
-            const R Pp = s_P[c1];
-            const R hold = SP::load(hin, (long long)ko * N + xi, wk * Pp);
-            const R bz = (L::D == 3) ? s_bz[c1] : R(0);
-            val = (R(1) - omh) * hold + wk * (omh * Pp - edot<L>(k, s_bx[c1], s_by[c1], bz));
-        } else {
-            const int sx = map_coord(ux, P.nx, P.bc[0]);
-            const int sy = map_coord(uy, P.ny, P.bc[1]);
-            const int sz = (L::D == 3) ? map_coord(uz, P.nz, P.bc[2]) : 0;
-            const long long si = ((long long)sz * P.ny + sy) * P.nx + sx;
-            const int o1 = c1 - (L::ex(k) + T::X1 * (L::ey(k) + T::Y1 * L::ez(k)));
-            const R Pp = s_P[o1];
-            const R hold = SP::load(hin, (long long)k * N + si, wk * Pp);
-            const R bz = (L::D == 3) ? s_bz[o1] : R(0);
-            val = (R(1) - omh) * hold + wk * (omh * Pp + edot<L>(k, s_bx[o1], s_by[o1], bz));
-        }
-        v[k] = val;
-        sum += val;
-    }
-    c_np1[xi] = sum;
-    if (SP::deviation) {
-        const R phin = phi_np1[xi];
-        const R Pn = p_term(P, phin, closure_mu(P, phin, sum));
-        SP::store(hout, xi, v[0], sum - (R(1) - w0) * Pn);
-#pragma unroll
-        for (int k = 1; k < L::Q; ++k) SP::store(hout, (long long)k * N + xi, v[k], R(L::w(k)) * Pn);
-    } else {
-#pragma unroll
-        for (int k = 0; k < L::Q; ++k) SP::store(hout, (long long)k * N + xi, v[k], R(0));
-    }
+    march<L, SP, BY, ZCH, false, WALLS>(K, hin, hout, phi_n, phi_np1, c_n, c_np1);
 }
 
 // ---- initialisation -------------------------------------------------------------------
@@ -435,10 +665,12 @@ k_c_step(const StepParams P, const typename SP::store_t* __restrict__ hin,
 // start values in the compute type.
 
 template <class L, class SP>
-__global__ void k_init(const StepParams P, const typename SP::real* __restrict__ phi,
+__global__ void k_init(const KParams K, const typename SP::real* __restrict__ phi,
                        const typename SP::real* __restrict__ c, typename SP::store_t* __restrict__ g,
                        typename SP::store_t* __restrict__ h) {
     using R = typename SP::real;
+    const StepParams& P = K.P;
+    const Coef<R>& C = coef<R>(K);
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= P.N) return;
     const int x = (int)(i % P.nx);
@@ -459,20 +691,20 @@ __global__ void k_init(const StepParams P, const typename SP::real* __restrict__
         gy += cw * R(L::ey(k)) * dk;
         gz += cw * R(L::ez(k)) * dk;
     }
-    const R inv = rsqrt_reg<R>(gx * gx + gy * gy + gz * gz, R(P.eps2));
+    const R inv = rsqrt_reg<R>(gx * gx + gy * gy + gz * gz, C.eps2);
     const R ph = phi[i], cc = c[i];
-    const R mu = closure_mu(P, ph, cc);
-    const R A = g_isotropic(P, ph, mu);
-    const R kct = P.counter_term ? (R(4) / R(P.W)) * ph * (R(1) - ph) * inv : R(0);
-    const R Pt = p_term(P, ph, mu);
-    const R f = mu * R(P.D_l - P.D_s);
+    const R mu = closure_mu(C, ph, cc);
+    const R A = g_isotropic(C, ph, mu);
+    const R kct = C.kct * ph * (R(1) - ph) * inv;
+    const R Pt = p_term(C, ph, mu);
+    const R f = mu * C.Dp;
     const R w0 = R(L::w(0));
 #pragma unroll
     for (int k = 0; k < L::Q; ++k) {
         const R wk = R(L::w(k));
         const R Gk = wk * (A + kct * edot<L>(k, gx, gy, gz));
         SP::store(g, (long long)k * P.N + i, wk * ph - R(0.5) * Gk, wk * ph);
-        const R Hk = R(P.gamma) * wk * f * edot<L>(k, gx, gy, gz);
+        const R Hk = C.gamma * wk * f * edot<L>(k, gx, gy, gz);
         const R heq = (k == 0) ? cc - (R(1) - w0) * Pt : wk * Pt;
         SP::store(h, (long long)k * P.N + i, heq - R(0.5) * Hk, heq);
     }
@@ -487,8 +719,9 @@ __global__ void k_from_f64(const double* __restrict__ src, R* __restrict__ dst, 
 }
 
 template <typename R>
-__global__ void k_fields_out(const StepParams P, const R* __restrict__ phi, const R* __restrict__ c,
+__global__ void k_fields_out(const KParams K, const R* __restrict__ phi, const R* __restrict__ c,
                              double* __restrict__ ophi, double* __restrict__ oc, double* __restrict__ omu) {
+    const StepParams& P = K.P;
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= P.N) return;
     const double ph = (double)phi[i], cc = (double)c[i];
@@ -499,15 +732,17 @@ __global__ void k_fields_out(const StepParams P, const R* __restrict__ phi, cons
 
 // Expand stored populations to FP64 (deviation modes add their references back).
 template <class L, class SP>
-__global__ void k_pops_out(const StepParams P, const typename SP::real* __restrict__ phi,
+__global__ void k_pops_out(const KParams K, const typename SP::real* __restrict__ phi,
                            const typename SP::real* __restrict__ c, const typename SP::store_t* __restrict__ g,
                            const typename SP::store_t* __restrict__ h, double* __restrict__ og,
                            double* __restrict__ oh) {
     using R = typename SP::real;
+    const StepParams& P = K.P;
+    const Coef<R>& C = coef<R>(K);
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= P.N) return;
     const R ph = phi[i], cc = c[i];
-    const R Pt = p_term(P, ph, closure_mu(P, ph, cc));
+    const R Pt = p_term(C, ph, closure_mu(C, ph, cc));
     const R w0 = R(L::w(0));
 #pragma unroll
     for (int k = 0; k < L::Q; ++k) {
