@@ -1,7 +1,7 @@
 """Benchmark of the coupled phi-mu LBM step on one GB300 (or N independent replicas).
 
 Workload: 256^3 synthetic porous medium (Gaussian random field, porosity 0.35,
-W = 2, D_l = 0.1, D_s = 0 with anti-trapping, counter term on), D3Q19, FP32
+W = 3, D_l = 0.1, D_s = 0 with anti-trapping, counter term on), D3Q19, FP32
 storage and arithmetic.  One "step" is one coupled time step n -> n+1 (the phi
 kernel and the composition kernel).  The state (2.6 GB) is far larger than L2.
 
@@ -323,7 +323,7 @@ def run_ours(args):
                "dtype": {"fp32": "f32", "fp64": "f64", "fp16dev": "f32 (f16 deviation storage)",
                          "bf16dev": "f32 (bf16 deviation storage)"}[prec],
                "data": "synthetic",
-               "config": {"workload": wl, "nodes": N, "lattice": "D3Q19", "porosity": 0.35, "W": 2.0,
+               "config": {"workload": wl, "nodes": N, "lattice": "D3Q19", "porosity": 0.35, "W": model.W,
                           "D_l": 0.1, "D_s": 0.0, "counter_term": 1, "anti_trapping": 1,
                           "parallelism": "replicas" if world > 1 else "single GPU",
                           "l2": "state %.1f GB per buffer set, larger than L2 (no flush needed)"
