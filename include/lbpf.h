@@ -152,6 +152,35 @@ lbpf_status lbpf_step_timed(lbpf_ctx *ctx, int64_t nsteps, double *kernel_ms);
  * Needs no GPU.  Errors: EINVAL for an unknown lattice or q == NULL. */
 lbpf_status lbpf_lattice_info(int32_t lattice, int32_t *q, int32_t *e, double *w);
 
+/* Largest n that lbpf_mass_noalloc accepts: 4096 blocks x 16384 elements. */
+#define LBPF_NOALLOC_MAX_ELEMENTS 67108864LL
+
+/* The sums of lbpf_mass (sum c, sum phi, count of bad nodes) over caller-owned
+ * device arrays, without allocating anything.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc, such as code
+ * running inside a host callback or a CUDA-graph node where allocation is not
+ * allowed, a monitor that must never block on the allocator, or an embedding
+ * runtime that owns all device memory.
+ *   c, phi      device arrays of n elements, FP64 (precision = LBPF_FP64) or FP32
+ *               (precision = LBPF_FP32), e.g. fields from lbpf_get_fields.
+ *   out_device  device array of 3 doubles: sum c, sum phi, and the number of
+ *               elements that are non-finite or have phi outside [-0.5, 1.5].
+ *   cuda_stream the stream the two kernels are queued on (NULL = default);
+ *               the call returns without synchronising.
+ * Scratch: a file-scope device array of 4096 x 3 doubles (96 KiB), present on
+ * every GPU that loads the library until the process exits.  The first call on
+ * a device looks up that array's device address (cudaGetSymbolAddress) and
+ * caches it, so make the first call on each device before any stream capture.
+ * Every call shares the array and leaves its partial sums in it; nothing in it
+ * needs clearing, because each call overwrites the slots it reads.  Calls whose
+ * kernels overlap on the GPU (other streams, other threads) race on the array
+ * and must be serialised by the caller.
+ * Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ * Errors (message in lbpf_last_error(NULL)): EINVAL for NULL pointers, n < 0,
+ * n > LBPF_NOALLOC_MAX_ELEMENTS or another precision; ECUDA. */
+lbpf_status lbpf_mass_noalloc(const void *c, const void *phi, int64_t n, int32_t precision,
+                              double *out_device, void *cuda_stream);
+
 /* Number of coupled steps taken since creation. */
 lbpf_status lbpf_get_step(const lbpf_ctx *ctx, int64_t *step);
 

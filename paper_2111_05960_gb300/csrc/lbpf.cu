@@ -26,6 +26,8 @@ struct Dispatch;
 
 }  // namespace
 
+void lbpf_internal_set_thread_error(const std::string& msg) { g_thread_error = msg; }
+
 struct lbpf_ctx {
     lbpf_params p;
     StepParams sp;

@@ -803,7 +803,7 @@ k_mass_partial(const R* __restrict__ c, const R* __restrict__ phi, long long n, 
     }
 }
 
-__global__ void __launch_bounds__(kMassThreads)
+static __global__ void __launch_bounds__(kMassThreads)
 k_mass_final(const double* __restrict__ partials, int nblocks, double* __restrict__ out) {
     double sc = 0.0, sp = 0.0, bad = 0.0;
     for (int b = threadIdx.x; b < nblocks; b += kMassThreads) {

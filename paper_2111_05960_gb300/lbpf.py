@@ -74,6 +74,7 @@ def load() -> ctypes.CDLL:
         "lbpf_destroy": [_vp],
         "lbpf_lattice_info": [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                               ctypes.POINTER(ctypes.c_int32), _dp],
+        "lbpf_mass_noalloc": [_vp, _vp, ctypes.c_int64, ctypes.c_int32, _vp, _vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -89,7 +90,7 @@ def exported_symbols():
     """Names declared in include/lbpf.h that the loaded library must export."""
     return ["lbpf_default_params", "lbpf_create", "lbpf_step", "lbpf_step_timed", "lbpf_mass",
             "lbpf_get_fields", "lbpf_get_populations", "lbpf_get_step", "lbpf_destroy",
-            "lbpf_last_error", "lbpf_lattice_info"]
+            "lbpf_last_error", "lbpf_lattice_info", "lbpf_mass_noalloc"]
 
 
 def _check(status: int, ctx=None):
@@ -166,6 +167,18 @@ def lbpf_destroy(ctx) -> None:
 def lbpf_last_error(ctx=None) -> str:
     m = load().lbpf_last_error(ctx)
     return m.decode() if m else ""
+
+
+NOALLOC_MAX_ELEMENTS = 67108864
+
+
+def lbpf_mass_noalloc(c_dev, phi_dev, n: int, precision: int, out_dev, cuda_stream=None) -> None:
+    """Sums of c and phi over caller-owned device arrays into out_dev (3 doubles on
+    the device), with no allocation; see include/lbpf.h.  Queued on cuda_stream."""
+    cp = c_dev.data_ptr() if hasattr(c_dev, "data_ptr") else int(c_dev)
+    pp = phi_dev.data_ptr() if hasattr(phi_dev, "data_ptr") else int(phi_dev)
+    op = out_dev.data_ptr() if hasattr(out_dev, "data_ptr") else int(out_dev)
+    _check(load().lbpf_mass_noalloc(cp, pp, int(n), int(precision), op, cuda_stream or None))
 
 
 def lbpf_lattice_info(lattice: int):
