@@ -156,6 +156,22 @@ class Oracle:
             raise MemoryError("oracle init failed")
         self.t = 0
 
+    @classmethod
+    def from_state(cls, p: OracleParams, g: np.ndarray, h: np.ndarray, phi: np.ndarray,
+                   c: np.ndarray) -> "Oracle":
+        """An oracle whose state is given directly: populations g, h [q, nz, ny, nx]
+        (after streaming, before the next collision) and the fields phi, c."""
+        o = cls.__new__(cls)
+        o.p = p
+        o._cp = p._c()
+        o.q = 19 if p.dim == 3 else 9
+        o.g = np.ascontiguousarray(g, dtype=np.float64).reshape((o.q,) + p.shape).copy()
+        o.h = np.ascontiguousarray(h, dtype=np.float64).reshape((o.q,) + p.shape).copy()
+        o.phi = np.ascontiguousarray(phi, dtype=np.float64).reshape(p.shape).copy()
+        o.c = np.ascontiguousarray(c, dtype=np.float64).reshape(p.shape).copy()
+        o.t = 0
+        return o
+
     def step(self, n: int = 1) -> "Oracle":
         rc = _load().or_step(ctypes.byref(self._cp), _dp(self.g), _dp(self.h),
                              _dp(self.phi), _dp(self.c), int(n))

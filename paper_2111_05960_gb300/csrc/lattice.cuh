@@ -1,6 +1,13 @@
 // Lattice tables of the coupled phi-mu LBM step, as compile-time functions so
 // that fully unrolled loops over k fold every e_k and w_k into constants.
 //
+// The kernels apply the weights as w_k = m_k / 36: a per-node quantity X is
+// divided by 36 once (correctly rounded) and the moving links multiply it by
+// m_k in {1, 2, 4}, which is exact.  With FP32 constants fl(1/18), fl(1/36),
+// fl(1/3) the weights do not sum to one (the D3Q19 moving weights exceed
+// 1 - fl(1/3) by 4.5e-8), and that offset would leak solute at every node and
+// step; with integer m_k the only errors left are unbiased roundings.
+//
 // D2Q9 follows the ordering of Sec. 3.1 (LBM notations): e0 = 0,
 // e1..e4 = (1,0),(0,1),(-1,0),(0,-1), e5..e8 = (1,1),(-1,1),(-1,-1),(1,-1),
 // w = 4/9, 1/9, 1/36.  D3Q19 (named among the lattices of the paper's code in
@@ -26,6 +33,8 @@ struct D2Q9 {
     __host__ __device__ static constexpr int opp(int k) {
         return k == 0 ? 0 : (k <= 4 ? ((k + 1) % 4) + 1 : ((k - 5 + 2) % 4) + 5);
     }
+    // w_k = m_k / 36 with integer m_k; the moving links have power-of-two m_k
+    __host__ __device__ static constexpr int m(int k) { return k == 0 ? 16 : (k <= 4 ? 4 : 1); }
 };
 
 struct D3Q19 {
@@ -52,6 +61,8 @@ struct D3Q19 {
     __host__ __device__ static constexpr int opp(int k) {
         return k == 0 ? 0 : ((k & 1) ? k + 1 : k - 1);
     }
+    // w_k = m_k / 36 with integer m_k; the moving links have power-of-two m_k
+    __host__ __device__ static constexpr int m(int k) { return k == 0 ? 12 : (k <= 6 ? 2 : 1); }
 };
 
 }  // namespace lbpf

@@ -155,7 +155,7 @@ struct Impl {
     static void launch_init(lbpf_ctx* ctx) {
         const long long N = ctx->sp.N;
         k_init<L, SP><<<(unsigned)((N + 255) / 256), 256, 0, ctx->stream>>>(
-            ctx->kp, (const R*)ctx->phi[ctx->cur], (const R*)ctx->c[ctx->cur], (S*)ctx->g[ctx->cur],
+            ctx->kp, (const R*)ctx->phi[ctx->cur], (R*)ctx->c[ctx->cur], (S*)ctx->g[ctx->cur],
             (S*)ctx->h[ctx->cur]);
     }
     static void launch_pops_out(lbpf_ctx* ctx, double* g, double* h) {

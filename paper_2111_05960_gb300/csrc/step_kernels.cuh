@@ -61,6 +61,8 @@ struct StepParams {
 template <typename R>
 struct Coef {
     R mu_eq, c_l, c_s, kS, kst, kdw, kct, D_l, D_s, Dp, gamma, atk, omg, omh, eps2;
+    R kct36;   // (1 - w_g/2) kct / 36: the counter-term vector per unit m_k
+    R kh36;    // (1 - w_h/2) gamma / 36: the flux vector of H per unit m_k
 };
 
 template <typename R>
@@ -75,6 +77,8 @@ __host__ Coef<R> make_coef(const StepParams& P) {
     c.gamma = R(P.gamma);
     c.atk = R(P.a_at * P.W * (P.c_s - P.c_l));
     c.omg = R(P.omg); c.omh = R(P.omh); c.eps2 = R(P.eps2);
+    c.kct36 = R((1.0 - 0.5 * P.omg) * (P.counter_term ? 4.0 / P.W : 0.0) / 36.0);
+    c.kh36 = R((1.0 - 0.5 * P.omh) * P.gamma / 36.0);
     return c;
 }
 
@@ -347,12 +351,12 @@ __device__ __forceinline__ void phi_ingredients(const StepParams& P, const Coef<
         const R mu = closure_mu(C, ph, cst[s]);
         const R A = g_isotropic(C, ph, mu);
         V4<R> v;
-        v.a = C.omg * ph + half_src * A;
+        v.a = (C.omg * ph + half_src * A) / R(36);      // per unit m_k (w_k = m_k / 36)
         if (P.counter_term) {
             R gx, gy, gz_;
             plane_gradient<L, BY>(pm, p0, pp, c2, gx, gy, gz_);
             const R inv = rsqrt_reg<R>(gx * gx + gy * gy + gz_ * gz_, C.eps2);
-            const R k = half_src * C.kct * ph * (R(1) - ph) * inv;   // (4/W) phi (1 - phi) n
+            const R k = C.kct36 * ph * (R(1) - ph) * inv;   // (4/W) phi (1 - phi) n, per unit m_k
             v.b = k * gx; v.c = k * gy; v.d = k * gz_;
         } else {
             v.b = v.c = v.d = R(0);
@@ -369,7 +373,6 @@ __device__ __forceinline__ void c_ingredients(const StepParams& P, const Coef<R>
                                               const R* pm, const R* p0, const R* pp, V4<R>* ing) {
     using G = Geo<L, BY>;
     const int tid = threadIdx.x + G::BX * threadIdx.y;
-    const R kk = (R(1) - R(0.5) * C.omh) * C.gamma;
     constexpr int IT = (G::P1 + G::NT - 1) / G::NT;
 #pragma unroll
     for (int it = 0; it < IT; ++it) {
@@ -385,8 +388,9 @@ __device__ __forceinline__ void c_ingredients(const StepParams& P, const Coef<R>
         const R inv = rsqrt_reg<R>(gx * gx + gy * gy + gz_ * gz_, C.eps2);
         const R f = mu * C.Dp + C.atk * dphi * inv;        // F = (mu D' + j_at / |grad|) grad
         V4<R> v;
-        v.a = p_term(C, ph, mu);
-        v.b = kk * f * gx; v.c = kk * f * gy; v.d = kk * f * gz_;
+        v.a = p_term(C, ph, mu) / R(36);                 // P per unit m_k
+        const R ff = C.kh36 * f;
+        v.b = ff * gx; v.c = ff * gy; v.d = ff * gz_;
         ing[s] = v;
     }
 }
@@ -486,11 +490,16 @@ __device__ __forceinline__ void pull_combine(const KParams& K, const Coef<typena
     typename SP::store_t* out = fout + xi;
 
     R v[L::Q];
+    // phi: a plain running sum.  c: a compensated sum (Fast2Sum, the rest
+    // population first), because the collision uses the stored c as the zeroth
+    // moment of h^eq: a plain FP32 sum is biased by about -1e-8 per node and
+    // step, which would leak that much solute every step.
     R sum = R(0);
+    R comp = R(0);
     constexpr int k0 = IS_PHI ? 0 : 1;
     if (!IS_PHI) {
         // rest population of h: h*_0 = (1 - w_h) h_0 + w_h h^eq_0 (H_0 = 0)
-        const R heq0 = st.cx - (R(1) - R(L::w(0))) * i0[c1].a;
+        const R heq0 = st.cx - R(36 - L::m(0)) * i0[c1].a;   // h^eq_0 = c - (1 - w_0) P
         v[0] = keep * (SP::deviation ? st.old[0] + heq0 : st.old[0]) + om * heq0;
         sum = v[0];
         if (!hold) SP::store(out, K.kN[0], v[0], R(0));
@@ -498,6 +507,7 @@ __device__ __forceinline__ void pull_combine(const KParams& K, const Coef<typena
 #pragma unroll
     for (int k = k0; k < L::Q; ++k) {
         const R wk = R(L::w(k));
+        const R mk = R(L::m(k));
         const bool wall = WALLS && ((st.wallmask >> k) & 1u);
         const V4<R>* ik = L::ez(k) > 0 ? im : (L::ez(k) < 0 ? ip : i0);   // upstream plane z - ez
         const R* fk = L::ez(k) > 0 ? fm : (L::ez(k) < 0 ? fp : f0);
@@ -505,15 +515,22 @@ __device__ __forceinline__ void pull_combine(const KParams& K, const Coef<typena
         const R sgn = wall ? R(-1) : R(1);
         R f_old = st.old[k];
         if (SP::deviation) {
-            const R ref = IS_PHI ? wk * (wall ? f0[c2] : fk[c2 - L::ex(k) - G::X2 * L::ey(k)]) : wk * g.a;
+            const R ref = IS_PHI ? wk * (wall ? f0[c2] : fk[c2 - L::ex(k) - G::X2 * L::ey(k)]) : mk * g.a;
             f_old += ref;
         }
         const R a = IS_PHI ? g.a : om * g.a;
-        const R val = keep * f_old + wk * (a + sgn * edot<L>(k, g.b, g.c, g.d));
+        const R val = keep * f_old + mk * (a + sgn * edot<L>(k, g.b, g.c, g.d));
         v[k] = val;
-        sum += val;
+        if (IS_PHI) {
+            sum += val;
+        } else {
+            const R t = sum + val;
+            comp += (sum - t) + val;
+            sum = t;
+        }
         if (!hold) SP::store(out, K.kN[k], val, R(0));
     }
+    if (!IS_PHI) sum += comp;
     if (IS_PHI) {
         const R phin = sum + R(0.5) * sA[c1];     // Eq. Moment_Phi
         moment_out[xi] = phin;
@@ -525,10 +542,10 @@ __device__ __forceinline__ void pull_combine(const KParams& K, const Coef<typena
         moment_out[xi] = sum;                      // Eq. Moment0_LBM_Concent
         if (hold) {
             const R phin = phi_np1_in[xi];
-            const R Pn = p_term(C, phin, closure_mu(C, phin, sum));
-            SP::store(out, K.kN[0], v[0], sum - (R(1) - R(L::w(0))) * Pn);
+            const R Ps = p_term(C, phin, closure_mu(C, phin, sum)) / R(36);
+            SP::store(out, K.kN[0], v[0], sum - R(36 - L::m(0)) * Ps);
 #pragma unroll
-            for (int k = 1; k < L::Q; ++k) SP::store(out, K.kN[k], v[k], R(L::w(k)) * Pn);
+            for (int k = 1; k < L::Q; ++k) SP::store(out, K.kN[k], v[k], R(L::m(k)) * Ps);
         }
     }
 }
@@ -666,7 +683,7 @@ k_c_step(const KParams K, const typename SP::store_t* __restrict__ hin,
 
 template <class L, class SP>
 __global__ void k_init(const KParams K, const typename SP::real* __restrict__ phi,
-                       const typename SP::real* __restrict__ c, typename SP::store_t* __restrict__ g,
+                       typename SP::real* __restrict__ c, typename SP::store_t* __restrict__ g,
                        typename SP::store_t* __restrict__ h) {
     using R = typename SP::real;
     const StepParams& P = K.P;
@@ -696,18 +713,25 @@ __global__ void k_init(const KParams K, const typename SP::real* __restrict__ ph
     const R mu = closure_mu(C, ph, cc);
     const R A = g_isotropic(C, ph, mu);
     const R kct = C.kct * ph * (R(1) - ph) * inv;
-    const R Pt = p_term(C, ph, mu);
+    const R Ps = p_term(C, ph, mu) / R(36);
     const R f = mu * C.Dp;
-    const R w0 = R(L::w(0));
+    R hsum = R(0), hcomp = R(0);
 #pragma unroll
     for (int k = 0; k < L::Q; ++k) {
         const R wk = R(L::w(k));
         const R Gk = wk * (A + kct * edot<L>(k, gx, gy, gz));
         SP::store(g, (long long)k * P.N + i, wk * ph - R(0.5) * Gk, wk * ph);
         const R Hk = C.gamma * wk * f * edot<L>(k, gx, gy, gz);
-        const R heq = (k == 0) ? cc - (R(1) - w0) * Pt : wk * Pt;
-        SP::store(h, (long long)k * P.N + i, heq - R(0.5) * Hk, heq);
+        const R heq = (k == 0) ? cc - R(36 - L::m(0)) * Ps : R(L::m(k)) * Ps;
+        const R hk = heq - R(0.5) * Hk;
+        SP::store(h, (long long)k * P.N + i, hk, heq);
+        const R t = hsum + hk;              // Fast2Sum: h_0 (the largest) comes first
+        hcomp += (hsum - t) + hk;
+        hsum = t;
     }
+    // the c field is the zeroth moment of the stored populations, so that the
+    // mass at step 0 is the populations' mass
+    c[i] = hsum + hcomp;
 }
 
 // ---- conversions and exports -----------------------------------------------------------
@@ -742,13 +766,12 @@ __global__ void k_pops_out(const KParams K, const typename SP::real* __restrict_
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= P.N) return;
     const R ph = phi[i], cc = c[i];
-    const R Pt = p_term(C, ph, closure_mu(C, ph, cc));
-    const R w0 = R(L::w(0));
+    const R Ps = p_term(C, ph, closure_mu(C, ph, cc)) / R(36);
 #pragma unroll
     for (int k = 0; k < L::Q; ++k) {
         const R wk = R(L::w(k));
         if (og) og[(long long)k * P.N + i] = (double)SP::load(g, (long long)k * P.N + i, wk * ph);
-        const R heq = (k == 0) ? cc - (R(1) - w0) * Pt : wk * Pt;
+        const R heq = (k == 0) ? cc - R(36 - L::m(0)) * Ps : R(L::m(k)) * Ps;
         if (oh) oh[(long long)k * P.N + i] = (double)SP::load(h, (long long)k * P.N + i, heq);
     }
 }

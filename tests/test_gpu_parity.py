@@ -130,3 +130,61 @@ def test_device_pointers_roundtrip():
     o = O.Oracle(to_oracle(m), phi0, c0).step(10)
     sim.close()
     assert rel_err(out.cpu().numpy(), o.phi) < FP64_TOL
+
+
+# 3-D shapes with interior blocks (x0 = 32 .. 64 of 70), interior rows and three
+# 16-plane z-chunks: the interior fast path and the chunk seams of the z-march
+@pytest.mark.parametrize("bc,ct", [((0, 0, 0), 1), ((1, 0, 1), 0), ((0, 1, 0), 1)])
+def test_fp64_3d_interior_blocks_and_z_chunks(bc, ct):
+    m, phi0, c0 = _case((40, 20, 70), seed=77 + ct, bc=bc, counter_term=ct)
+    sim = L.Simulation(m, phi0, c0, precision="fp64")
+    sim.step(20)
+    phi, c, mu = sim.fields()
+    g, h = sim.populations()
+    sim.close()
+    o = O.Oracle(to_oracle(m), phi0, c0).step(20)
+    errs = dict(phi=rel_err(phi, o.phi), c=rel_err(c, o.c), mu=rel_err(mu, o.mu),
+                g=max(rel_err(g[k], o.g[k]) for k in range(19)),
+                h=max(rel_err(h[k], o.h[k]) for k in range(19)))
+    assert max(errs.values()) < FP64_TOL, errs
+
+
+def test_fp32_3d_error_against_fp64_oracle():
+    m, phi0, c0 = _case((40, 20, 70), seed=5, bc=(0, 0, 0))
+    errs = _compare(m, phi0, c0, 50, precision="fp32", pops=False)
+    assert errs["phi"] < 2e-5 and errs["c"] < 2e-5, errs
+
+
+def test_from_state_continues_the_oracle():
+    """Oracle.from_state(state) steps exactly like the oracle that produced the state
+    (the full-size check below relies on it)."""
+    m, phi0, c0 = _case((1, 12, 20), seed=4)
+    a = O.Oracle(to_oracle(m), phi0, c0).step(3)
+    b = O.Oracle.from_state(to_oracle(m), a.g, a.h, a.phi, a.c)
+    a.step(2)
+    b.step(2)
+    assert np.array_equal(a.phi, b.phi) and np.array_equal(a.h, b.h)
+
+
+@pytest.mark.slow
+def test_full_size_bench_configuration_one_step():
+    """256^3 porous medium, D3Q19, FP32: the launch configuration the benchmark times.
+    After a few GPU steps, the oracle takes one FP64 step from the GPU's own state
+    (populations and fields, exported exactly) and the GPU takes the same step in
+    FP32; every output agrees to the FP32 rounding of one step."""
+    m, phi0, c0 = WL.porous_3d(n=256)
+    sim = L.Simulation(m, phi0, c0, precision="fp32")
+    sim.step(5)
+    g, h = sim.populations()
+    phi, c, _ = sim.fields()
+    o = O.Oracle.from_state(to_oracle(m), g, h, phi, c)
+    del g, h
+    sim.step(1)
+    phi1, c1, _ = sim.fields()
+    g1, h1 = sim.populations()
+    sim.close()
+    o.step(1)
+    assert rel_err(phi1, o.phi) < 1e-5
+    assert rel_err(c1, o.c) < 1e-5
+    assert max(rel_err(g1[k], o.g[k]) for k in range(19)) < 1e-5
+    assert max(rel_err(h1[k], o.h[k]) for k in range(19)) < 1e-5
