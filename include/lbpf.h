@@ -93,7 +93,8 @@ typedef struct {
     int32_t anti_trapping;       /* 1: j_at included in H_k */
     double a_at;                 /* a of j_at; < 0 selects (1 - D_s/D_l)/4 */
     double eps_n;                /* regularisation of |grad phi| in n; default 1e-12 */
-    int32_t mass_every;          /* reserved: steps between mass corrections, 0 = off */
+    int32_t mass_every;          /* steps between FP64 mass corrections, 0 = off (see
+                                    lbpf_solute_mass); FP32 and 16-bit modes want 1 */
     int32_t reserved;            /* set to 0 */
 } lbpf_params;
 
@@ -129,6 +130,23 @@ lbpf_status lbpf_step(lbpf_ctx *ctx, int64_t nsteps);
  * [-0.5, 1.5]. */
 lbpf_status lbpf_mass(lbpf_ctx *ctx, double *total_c, double *total_phi);
 
+/* Exact solute mass of the current state: the sum over nodes and directions of
+ * the h populations (their zeroth moment, Eq. Moment0_LBM_Concent), accumulated
+ * without rounding loss in FP64 (deviation modes add their references back).
+ * With mass_every > 0, *target (optional) receives the mass the correction
+ * holds: the exact population mass right after creation; else NaN.
+ *
+ * Mass correction (a build addition; the paper's FP64-free scheme has none):
+ * FP32 arithmetic rounds each collision at ~1e-7 relative, and nodes sitting on
+ * a binade boundary (c = 1 in the solid) round asymmetrically, so the total
+ * solute drifts by ~1e-9 per step.  With mass_every = k > 0, every k-th step the
+ * composition kernel also sums the exact mass it wrote (one FP64 value per
+ * block), a one-block kernel compares it with the target in FP64, and a third
+ * kernel adds the difference back to h_0 and c on a rotating subset of nodes
+ * (about 1e-5 per node, so each node's rounding is ~1% of it).  The next
+ * measurement sees any residual, so errors do not accumulate.  Synchronises. */
+lbpf_status lbpf_solute_mass(lbpf_ctx *ctx, double *mass, double *target);
+
 /* Copy phi, c and mu = mu_eq + c - c^co(phi) at the current step into FP64
  * arrays [nz][ny][nx] (any of them may be NULL).  Synchronises the stream. */
 lbpf_status lbpf_get_fields(lbpf_ctx *ctx, double *phi, double *c, double *mu,
@@ -142,7 +160,9 @@ lbpf_status lbpf_get_populations(lbpf_ctx *ctx, double *g, double *h, int32_t pt
 
 /* Time the kernels of nsteps steps with CUDA events recorded on the context's
  * stream around each launch.  kernel_ms[0] accumulates the phi kernel,
- * kernel_ms[1] the composition kernel, in milliseconds.  Synchronises. */
+ * kernel_ms[1] the composition kernel, kernel_ms[2] the mass-correction
+ * kernels (0 when mass_every = 0), in milliseconds; kernel_ms has 3 entries.
+ * Synchronises. */
 lbpf_status lbpf_step_timed(lbpf_ctx *ctx, int64_t nsteps, double *kernel_ms);
 
 /* Lattice table of the population ordering used by lbpf_get_populations:

@@ -43,6 +43,10 @@ struct lbpf_ctx {
     double* staging = nullptr;     // 3 N doubles, allocated on first host transfer
     double* partials = nullptr;    // mass reduction scratch
     double* mass_out = nullptr;    // 3 doubles
+    double* corr_partials = nullptr;   // one FP64 mass per composition-kernel block
+    MassCorr* corr = nullptr;          // closed-loop mass correction state (device)
+    int corr_blocks = 0;
+    long long corr_stride = 1;
     int mass_blocks = 0;
     int cur = 0;
     int64_t step = 0;
@@ -74,9 +78,12 @@ lbpf_status cuda_fail(lbpf_ctx* ctx, cudaError_t e, const char* what) {
 struct Dispatch {
     lbpf_status (*prepare)(lbpf_ctx*);
     void (*launch_phi)(lbpf_ctx*, int cur);
-    void (*launch_c)(lbpf_ctx*, int cur);
+    void (*launch_c)(lbpf_ctx*, int cur, double* mass_partials);
     void (*launch_init)(lbpf_ctx*);
     void (*launch_pops_out)(lbpf_ctx*, double* g, double* h);
+    void (*launch_corr)(lbpf_ctx*, int cur_after, long long offset);
+    void (*launch_pop_mass)(lbpf_ctx*);
+    int (*c_blocks)(const lbpf_ctx*);
 };
 
 // Tile shapes: 32 x BY threads per block, ZCH planes per block in 3-D, at least
@@ -99,6 +106,10 @@ struct Dispatch {
 #ifndef LBPF_MINB3_F64
 #define LBPF_MINB3_F64 2
 #endif
+// Increment per corrected node of the mass correction: ~100 ulps of an FP32
+// value near 1, so that each node's rounding is ~1% of the increment.
+constexpr double kCorrDelta = 1e-5;
+
 template <class L>
 struct TileCfg;
 template <>
@@ -145,12 +156,12 @@ struct Impl {
             ctx->kp, (const S*)ctx->g[cur], (S*)ctx->g[nxt], (const R*)ctx->phi[cur], (const R*)ctx->c[cur],
             (R*)ctx->phi[nxt]);
     }
-    static void launch_c(lbpf_ctx* ctx, int cur) {
+    static void launch_c(lbpf_ctx* ctx, int cur, double* mass_partials) {
         const int nxt = cur ^ 1;
         auto kern = walls(ctx) ? k_c_step<L, SP, BY, ZCH, MINB, true> : k_c_step<L, SP, BY, ZCH, MINB, false>;
         kern<<<grid(ctx), dim3(32, BY), smem_c, ctx->stream>>>(
             ctx->kp, (const S*)ctx->h[cur], (S*)ctx->h[nxt], (const R*)ctx->phi[cur], (const R*)ctx->phi[nxt],
-            (const R*)ctx->c[cur], (R*)ctx->c[nxt]);
+            (const R*)ctx->c[cur], (R*)ctx->c[nxt], mass_partials);
     }
     static void launch_init(lbpf_ctx* ctx) {
         const long long N = ctx->sp.N;
@@ -165,8 +176,27 @@ struct Impl {
             ctx->kp, (const R*)ctx->phi[cur], (const R*)ctx->c[cur], (const S*)ctx->g[cur],
             (const S*)ctx->h[cur], g, h);
     }
+    // mass correction after a composition step whose new state has parity `cur_after`
+    static void launch_corr(lbpf_ctx* ctx, int cur_after, long long offset) {
+        k_mass_corr_plan<<<1, kMassThreads, 0, ctx->stream>>>(ctx->corr_partials, ctx->corr_blocks, ctx->corr,
+                                                             ctx->sp.N, kCorrDelta);
+        k_mass_corr_apply<SP><<<64, 256, 0, ctx->stream>>>(ctx->corr, (R*)ctx->c[cur_after],
+                                                           (S*)ctx->h[cur_after], ctx->sp.N, offset,
+                                                           ctx->corr_stride);
+    }
+    static void launch_pop_mass(lbpf_ctx* ctx) {
+        k_pop_mass<L, SP><<<ctx->mass_blocks, kMassThreads, 0, ctx->stream>>>(
+            ctx->kp, (const R*)ctx->phi[ctx->cur], (const R*)ctx->c[ctx->cur], (const S*)ctx->h[ctx->cur],
+            ctx->partials);
+        k_mass_final<<<1, kMassThreads, 0, ctx->stream>>>(ctx->partials, ctx->mass_blocks, ctx->mass_out);
+    }
+    static int c_blocks(const lbpf_ctx* ctx) {
+        const dim3 g = grid(ctx);
+        return (int)(g.x * g.y * g.z);
+    }
     static const Dispatch* table() {
-        static const Dispatch d = {prepare, launch_phi, launch_c, launch_init, launch_pops_out};
+        static const Dispatch d = {prepare, launch_phi, launch_c, launch_init, launch_pops_out,
+                                   launch_corr, launch_pop_mass, c_blocks};
         return &d;
     }
 };
@@ -212,6 +242,7 @@ lbpf_status validate(const lbpf_params* p, std::string& why) {
         !std::isfinite(p->mu_eq) || !std::isfinite(p->a_at) || !(p->eps_n >= 0))
         return bad("non-finite parameter");
     if (p->anti_trapping && p->a_at < 0 && !(p->D_l > 0)) return bad("automatic a needs D_l > 0");
+    if (p->mass_every < 0) return bad("mass_every must be >= 0");
     return LBPF_OK;
 }
 
@@ -246,6 +277,27 @@ void free_all(lbpf_ctx* ctx) {
     }
     cudaFree(ctx->staging); cudaFree(ctx->partials); cudaFree(ctx->mass_out);
     ctx->staging = ctx->partials = ctx->mass_out = nullptr;
+    cudaFree(ctx->corr_partials); cudaFree(ctx->corr);
+    ctx->corr_partials = nullptr;
+    ctx->corr = nullptr;
+}
+
+// One coupled step (both kernels), followed by the mass correction when it is due.
+void launch_one_step(lbpf_ctx* ctx) {
+    const bool corr = ctx->corr && ((ctx->step + 1) % ctx->p.mass_every == 0);
+    ctx->ops->launch_phi(ctx, ctx->cur);
+    ctx->ops->launch_c(ctx, ctx->cur, corr ? ctx->corr_partials : nullptr);
+    if (corr) ctx->ops->launch_corr(ctx, ctx->cur ^ 1, (long long)((ctx->step * 7919LL) % ctx->sp.N));
+    ctx->cur ^= 1;
+    ctx->step += 1;
+}
+
+// A prime stride coprime with N for spreading the corrected nodes.
+long long corr_stride_for(long long N) {
+    const long long primes[] = {1000003LL, 998244353LL, 7919LL, 104729LL, 15485863LL};
+    for (long long p : primes)
+        if (N % p != 0) return p % N == 0 ? 1 : p;
+    return 1;
 }
 
 lbpf_status alloc(lbpf_ctx* ctx, void** ptr, size_t bytes, const char* what) {
@@ -395,6 +447,21 @@ lbpf_status lbpf_create(const lbpf_params* p, const double* phi0, const double* 
     ctx->cur = 0;
     ops->launch_init(ctx);
     if ((st = check_launch(ctx, "initialisation kernels")) != LBPF_OK) return abort_create(st);
+    if (p->mass_every > 0) {
+        // the correction holds the exact population mass of the initial state
+        ctx->corr_blocks = ops->c_blocks(ctx);
+        ctx->corr_stride = corr_stride_for(ctx->sp.N);
+        if ((st = alloc(ctx, (void**)&ctx->corr_partials, sizeof(double) * ctx->corr_blocks, "mass-correction partials")) != LBPF_OK)
+            return abort_create(st);
+        if ((st = alloc(ctx, (void**)&ctx->corr, sizeof(MassCorr), "mass-correction state")) != LBPF_OK)
+            return abort_create(st);
+        e = cudaMemsetAsync(ctx->corr, 0, sizeof(MassCorr), ctx->stream);
+        if (e != cudaSuccess) { cuda_fail(ctx, e, "mass-correction state"); return abort_create(LBPF_ECUDA); }
+        ops->launch_pop_mass(ctx);
+        e = cudaMemcpyAsync(&ctx->corr->target, ctx->mass_out, sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream);
+        if (e != cudaSuccess) { cuda_fail(ctx, e, "mass-correction target"); return abort_create(LBPF_ECUDA); }
+        if ((st = check_launch(ctx, "population mass kernels")) != LBPF_OK) return abort_create(st);
+    }
     e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) { cuda_fail(ctx, e, "initialisation"); return abort_create(LBPF_ECUDA); }
     *out = ctx;
@@ -405,12 +472,7 @@ lbpf_status lbpf_step(lbpf_ctx* ctx, int64_t nsteps) {
     if (!ctx) return fail(nullptr, LBPF_EINVAL, "ctx is NULL");
     if (ctx->poisoned) return fail(ctx, LBPF_ESTATE, "context poisoned by an earlier error");
     if (nsteps < 0) return fail(ctx, LBPF_EINVAL, "nsteps < 0");
-    for (int64_t s = 0; s < nsteps; ++s) {
-        ctx->ops->launch_phi(ctx, ctx->cur);
-        ctx->ops->launch_c(ctx, ctx->cur);
-        ctx->cur ^= 1;
-        ctx->step += 1;
-    }
+    for (int64_t s = 0; s < nsteps; ++s) launch_one_step(ctx);
     return check_launch(ctx, "step kernels");
 }
 
@@ -418,9 +480,9 @@ lbpf_status lbpf_step_timed(lbpf_ctx* ctx, int64_t nsteps, double* kernel_ms) {
     if (!ctx) return fail(nullptr, LBPF_EINVAL, "ctx is NULL");
     if (ctx->poisoned) return fail(ctx, LBPF_ESTATE, "context poisoned by an earlier error");
     if (nsteps < 0 || !kernel_ms) return fail(ctx, LBPF_EINVAL, "nsteps < 0 or kernel_ms NULL");
-    kernel_ms[0] = kernel_ms[1] = 0.0;
+    kernel_ms[0] = kernel_ms[1] = kernel_ms[2] = 0.0;
     if (nsteps == 0) return LBPF_OK;
-    std::vector<cudaEvent_t> ev(3 * nsteps, nullptr);
+    std::vector<cudaEvent_t> ev(4 * nsteps, nullptr);
     lbpf_status st = LBPF_OK;
     for (auto& x : ev) {
         cudaError_t e = cudaEventCreate(&x);
@@ -428,11 +490,14 @@ lbpf_status lbpf_step_timed(lbpf_ctx* ctx, int64_t nsteps, double* kernel_ms) {
     }
     if (st == LBPF_OK) {
         for (int64_t s = 0; s < nsteps; ++s) {
-            cudaEventRecord(ev[3 * s], ctx->stream);
+            const bool corr = ctx->corr && ((ctx->step + 1) % ctx->p.mass_every == 0);
+            cudaEventRecord(ev[4 * s], ctx->stream);
             ctx->ops->launch_phi(ctx, ctx->cur);
-            cudaEventRecord(ev[3 * s + 1], ctx->stream);
-            ctx->ops->launch_c(ctx, ctx->cur);
-            cudaEventRecord(ev[3 * s + 2], ctx->stream);
+            cudaEventRecord(ev[4 * s + 1], ctx->stream);
+            ctx->ops->launch_c(ctx, ctx->cur, corr ? ctx->corr_partials : nullptr);
+            cudaEventRecord(ev[4 * s + 2], ctx->stream);
+            if (corr) ctx->ops->launch_corr(ctx, ctx->cur ^ 1, (long long)((ctx->step * 7919LL) % ctx->sp.N));
+            cudaEventRecord(ev[4 * s + 3], ctx->stream);
             ctx->cur ^= 1;
             ctx->step += 1;
         }
@@ -440,11 +505,13 @@ lbpf_status lbpf_step_timed(lbpf_ctx* ctx, int64_t nsteps, double* kernel_ms) {
         cudaError_t e = cudaStreamSynchronize(ctx->stream);
         if (st == LBPF_OK && e != cudaSuccess) st = cuda_fail(ctx, e, "step synchronisation");
         for (int64_t s = 0; st == LBPF_OK && s < nsteps; ++s) {
-            float a = 0.f, b = 0.f;
-            cudaEventElapsedTime(&a, ev[3 * s], ev[3 * s + 1]);
-            cudaEventElapsedTime(&b, ev[3 * s + 1], ev[3 * s + 2]);
+            float a = 0.f, b = 0.f, c = 0.f;
+            cudaEventElapsedTime(&a, ev[4 * s], ev[4 * s + 1]);
+            cudaEventElapsedTime(&b, ev[4 * s + 1], ev[4 * s + 2]);
+            cudaEventElapsedTime(&c, ev[4 * s + 2], ev[4 * s + 3]);
             kernel_ms[0] += a;
             kernel_ms[1] += b;
+            kernel_ms[2] += c;
         }
     }
     for (auto& x : ev) if (x) cudaEventDestroy(x);
@@ -469,6 +536,23 @@ lbpf_status lbpf_mass(lbpf_ctx* ctx, double* total_c, double* total_phi) {
                  hostv[2], (long long)ctx->step);
         return fail(ctx, LBPF_EUNSTABLE, buf);
     }
+    return LBPF_OK;
+}
+
+lbpf_status lbpf_solute_mass(lbpf_ctx* ctx, double* mass, double* target) {
+    if (!ctx || !mass) return fail(ctx, LBPF_EINVAL, "NULL argument");
+    if (ctx->poisoned) return fail(ctx, LBPF_ESTATE, "context poisoned by an earlier error");
+    ctx->ops->launch_pop_mass(ctx);
+    lbpf_status st = check_launch(ctx, "population mass kernels");
+    if (st != LBPF_OK) return st;
+    double hostv[3];
+    LBPF_CUDA(ctx, cudaMemcpyAsync(hostv, ctx->mass_out, sizeof(hostv), cudaMemcpyDeviceToHost, ctx->stream));
+    double tgt = 0.0;
+    if (ctx->corr)
+        LBPF_CUDA(ctx, cudaMemcpyAsync(&tgt, &ctx->corr->target, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    LBPF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    *mass = hostv[0];
+    if (target) *target = ctx->corr ? tgt : std::nan("");
     return LBPF_OK;
 }
 

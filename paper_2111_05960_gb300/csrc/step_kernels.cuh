@@ -403,6 +403,19 @@ __device__ __forceinline__ void c_ingredients(const StepParams& P, const Coef<R>
 // upstream node is inside, so the source is xi + koff[k] (one add).  Otherwise
 // the wrapped x index, row and plane offsets for e = -1, 0, 1 are computed once
 // and a link's source costs two adds and no branch.
+// Exact solute mass of the populations a thread has written, as an unevaluated
+// sum hi + lo (float-float in FP32), reduced per block in FP64 at the end.
+template <typename R>
+struct MassAcc {
+    R hi, lo;
+    __device__ __forceinline__ void add(R s, R e) {      // add s + e (e small)
+        const R t = hi + s;
+        const R bb = t - hi;
+        lo += ((hi - (t - bb)) + (s - bb)) + e;          // TwoSum error of hi + s
+        hi = t;
+    }
+};
+
 template <class L, class SP, bool IS_PHI, bool WALLS>
 struct PullState {
     using R = typename SP::real;
@@ -476,7 +489,8 @@ __device__ __forceinline__ void pull_combine(const KParams& K, const Coef<typena
                                              const typename SP::real* sA,
                                              const typename SP::real* __restrict__ phi_np1_in,
                                              typename SP::real* __restrict__ moment_out,
-                                             const PullState<L, SP, IS_PHI, WALLS>& st) {
+                                             const PullState<L, SP, IS_PHI, WALLS>& st,
+                                             MassAcc<typename SP::real>& macc) {
     using R = typename SP::real;
     using G = Geo<L, BY>;
     const long long xi = st.xi;
@@ -530,7 +544,10 @@ __device__ __forceinline__ void pull_combine(const KParams& K, const Coef<typena
         }
         if (!hold) SP::store(out, K.kN[k], val, R(0));
     }
-    if (!IS_PHI) sum += comp;
+    if (!IS_PHI) {
+        macc.add(sum, comp);   // the node's exact population mass is sum + comp
+        sum += comp;
+    }
     if (IS_PHI) {
         const R phin = sum + R(0.5) * sA[c1];     // Eq. Moment_Phi
         moment_out[xi] = phin;
@@ -550,14 +567,34 @@ __device__ __forceinline__ void pull_combine(const KParams& K, const Coef<typena
     }
 }
 
-// One z-marching pass of either kernel.
+// FP64 block sum of the threads' mass accumulators, written to
+// partials[linear block index] (all threads of the block must call it).
+template <int NT, typename R>
+__device__ __forceinline__ void block_mass_out(const MassAcc<R>& m, double* __restrict__ partials) {
+    __shared__ double red[NT / 32];
+    double v = (double)m.hi + (double)m.lo;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int tid = threadIdx.x + 32 * threadIdx.y;
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0;
+        for (int w = 0; w < NT / 32; ++w) t += red[w];
+        partials[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = t;
+    }
+}
+
+// One z-marching pass of either kernel.  The composition kernel also sums the
+// exact mass of the populations it writes into mass_partials (one FP64 value
+// per block) when that pointer is not null.
 template <class L, class SP, int BY, int ZCH, bool IS_PHI, bool WALLS>
 __device__ __forceinline__ void march(const KParams& K, const typename SP::store_t* __restrict__ fin,
                                       typename SP::store_t* __restrict__ fout,
                                       const typename SP::real* __restrict__ phi_n,
                                       const typename SP::real* __restrict__ phi_np1,
                                       const typename SP::real* __restrict__ c_n,
-                                      typename SP::real* __restrict__ moment_out) {
+                                      typename SP::real* __restrict__ moment_out,
+                                      double* __restrict__ mass_partials) {
     using R = typename SP::real;
     using G = Geo<L, BY>;
     const StepParams& P = K.P;
@@ -575,6 +612,7 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
     const bool inside2 = x0 >= 2 && x0 + G::BX + 2 <= P.nx && y0 >= 2 && y0 + BY + 2 <= P.ny;
     const bool inside1 = x0 >= 1 && x0 + G::BX + 1 <= P.nx && y0 >= 1 && y0 + BY + 1 <= P.ny;
     PullState<L, SP, IS_PHI, WALLS> st;
+    MassAcc<R> macc{R(0), R(0)};
 
     // the ring inputs of plane zg go to stage buffer zg & 1
     auto fetch_ring = [&](int zg) {
@@ -601,7 +639,8 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
         __syncthreads();
         if (active_xy)
             pull_combine<L, SP, BY, IS_PHI, WALLS>(K, C, fout, sing, sing, sing, sphi, sphi, sphi, sA, phi_np1,
-                                                   moment_out, st);
+                                                   moment_out, st, macc);
+        if (!IS_PHI && mass_partials) block_mass_out<G::NT>(macc, mass_partials);
         return;
     }
 
@@ -644,9 +683,10 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
             pull_combine<L, SP, BY, IS_PHI, WALLS>(K, C, fout, sing + islot(z - 1) * G::P1,
                                                    sing + islot(z) * G::P1, sing + islot(z + 1) * G::P1,
                                                    fslot(z - 1), fslot(z), fslot(z + 1), sA + islot(z) * G::P1,
-                                                   phi_np1, moment_out, st);
+                                                   phi_np1, moment_out, st, macc);
     }
     cp_async_wait_all();
+    if (!IS_PHI && mass_partials) block_mass_out<G::NT>(macc, mass_partials);
 }
 
 template <class L, class SP, int BY, int ZCH>
@@ -664,7 +704,7 @@ __global__ void __launch_bounds__(32 * BY, MINB)
 k_phi_step(const KParams K, const typename SP::store_t* __restrict__ gin,
            typename SP::store_t* __restrict__ gout, const typename SP::real* __restrict__ phi_n,
            const typename SP::real* __restrict__ c_n, typename SP::real* __restrict__ phi_np1) {
-    march<L, SP, BY, ZCH, true, WALLS>(K, gin, gout, phi_n, nullptr, c_n, phi_np1);
+    march<L, SP, BY, ZCH, true, WALLS>(K, gin, gout, phi_n, nullptr, c_n, phi_np1, nullptr);
 }
 
 template <class L, class SP, int BY, int ZCH, int MINB, bool WALLS>
@@ -672,8 +712,8 @@ __global__ void __launch_bounds__(32 * BY, MINB)
 k_c_step(const KParams K, const typename SP::store_t* __restrict__ hin,
          typename SP::store_t* __restrict__ hout, const typename SP::real* __restrict__ phi_n,
          const typename SP::real* __restrict__ phi_np1, const typename SP::real* __restrict__ c_n,
-         typename SP::real* __restrict__ c_np1) {
-    march<L, SP, BY, ZCH, false, WALLS>(K, hin, hout, phi_n, phi_np1, c_n, c_np1);
+         typename SP::real* __restrict__ c_np1, double* __restrict__ mass_partials) {
+    march<L, SP, BY, ZCH, false, WALLS>(K, hin, hout, phi_n, phi_np1, c_n, c_np1, mass_partials);
 }
 
 // ---- initialisation -------------------------------------------------------------------
@@ -839,6 +879,97 @@ k_mass_final(const double* __restrict__ partials, int nblocks, double* __restric
         out[0] = sc;
         out[1] = sp;
         out[2] = bad;
+    }
+}
+
+
+// ---- exact population mass and the closed-loop mass correction ------------------
+// The solute mass of a state is the sum of its h populations (the zeroth moment,
+// Eq. Moment0_LBM_Concent).  In FP32 the collision and the stored fields round
+// at ~1e-7 relative per value; near-stationary nodes whose values sit on a
+// binade boundary (c = 1 in the solid) round asymmetrically, so the total drifts
+// by ~1e-9 per step.  When enabled, the composition kernel sums the exact mass
+// of what it wrote (mass_partials), k_mass_corr_plan compares it with the
+// target in FP64, and k_mass_corr_apply adds the difference back to the rest
+// population and to c on a rotating subset of nodes, large enough per node
+// (~1e-5) to be represented with ~1% rounding.  The next step measures again,
+// so the residual never accumulates.
+
+struct MassCorr {
+    double target;      // mass to hold: the exact population mass at creation
+    double measured;    // exact population mass after the last measured step
+    double delta;       // increment per corrected node in the last correction
+    long long count;    // nodes corrected by the last correction
+};
+
+static __global__ void __launch_bounds__(kMassThreads)
+k_mass_corr_plan(const double* __restrict__ partials, int nblocks, MassCorr* __restrict__ mc, long long N,
+                 double delta_target) {
+    double sc = 0.0, d1 = 0.0, d2 = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += kMassThreads) sc += partials[b];
+    block_sum3<double>(sc, d1, d2);
+    if (threadIdx.x == 0) {
+        const double dM = mc->target - sc;
+        long long k = 0;
+        if (dM != 0.0) {
+            const double want = fabs(dM) / delta_target;
+            k = want < 1.0 ? 1 : (want > (double)N ? N : (long long)llrint(want));
+        }
+        mc->measured = sc;
+        mc->count = k;
+        mc->delta = k > 0 ? dM / (double)k : 0.0;
+    }
+}
+
+// Node j of the correction is (offset + j * stride) mod N; stride is a large
+// prime, offset rotates with the step so that no node is corrected repeatedly.
+template <class SP>
+__global__ void k_mass_corr_apply(const MassCorr* __restrict__ mc, typename SP::real* __restrict__ c,
+                                  typename SP::store_t* __restrict__ h0, long long N, long long offset,
+                                  long long stride) {
+    using R = typename SP::real;
+    const long long count = mc->count;
+    const R d = R(mc->delta);
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < count;
+         j += (long long)gridDim.x * blockDim.x) {
+        const long long i = (long long)(((unsigned long long)offset + (unsigned long long)j * (unsigned long long)stride) %
+                                        (unsigned long long)N);
+        c[i] += d;
+        // deviation storage: the stored h are deviations from references whose
+        // sum is c, so raising c raises the populations' sum by the same amount
+        if (!SP::deviation) {
+            R* hp = reinterpret_cast<R*>(h0);
+            hp[i] += d;
+        }
+    }
+}
+
+// Exact FP64 population mass: h_k expanded (deviation modes add their references
+// back), summed per node in float-float, per block in FP64.
+template <class L, class SP>
+__global__ void __launch_bounds__(kMassThreads)
+k_pop_mass(const KParams K, const typename SP::real* __restrict__ phi, const typename SP::real* __restrict__ c,
+           const typename SP::store_t* __restrict__ h, double* __restrict__ partials) {
+    using R = typename SP::real;
+    const StepParams& P = K.P;
+    const Coef<R>& C = coef<R>(K);
+    MassAcc<R> acc{R(0), R(0)};
+    for (long long i = blockIdx.x * (long long)kMassThreads + threadIdx.x; i < P.N;
+         i += (long long)gridDim.x * kMassThreads) {
+        const R ph = phi[i], cc = c[i];
+        const R Ps = p_term(C, ph, closure_mu(C, ph, cc)) / R(36);
+#pragma unroll
+        for (int k = 0; k < L::Q; ++k) {
+            const R ref = (k == 0) ? cc - R(36 - L::m(0)) * Ps : R(L::m(k)) * Ps;
+            acc.add(SP::load(h, (long long)k * P.N + i, ref), R(0));
+        }
+    }
+    double v = (double)acc.hi + (double)acc.lo, d1 = 0.0, d2 = 0.0;
+    block_sum3<double>(v, d1, d2);
+    if (threadIdx.x == 0) {
+        partials[3 * blockIdx.x + 0] = v;
+        partials[3 * blockIdx.x + 1] = 0.0;
+        partials[3 * blockIdx.x + 2] = 0.0;
     }
 }
 

@@ -75,6 +75,7 @@ def load() -> ctypes.CDLL:
         "lbpf_lattice_info": [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                               ctypes.POINTER(ctypes.c_int32), _dp],
         "lbpf_mass_noalloc": [_vp, _vp, ctypes.c_int64, ctypes.c_int32, _vp, _vp],
+        "lbpf_solute_mass": [_vp, _dp, _dp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -90,7 +91,7 @@ def exported_symbols():
     """Names declared in include/lbpf.h that the loaded library must export."""
     return ["lbpf_default_params", "lbpf_create", "lbpf_step", "lbpf_step_timed", "lbpf_mass",
             "lbpf_get_fields", "lbpf_get_populations", "lbpf_get_step", "lbpf_destroy",
-            "lbpf_last_error", "lbpf_lattice_info", "lbpf_mass_noalloc"]
+            "lbpf_last_error", "lbpf_lattice_info", "lbpf_mass_noalloc", "lbpf_solute_mass"]
 
 
 def _check(status: int, ctx=None):
@@ -134,9 +135,17 @@ def lbpf_step(ctx, nsteps: int) -> None:
 
 
 def lbpf_step_timed(ctx, nsteps: int):
-    ms = (ctypes.c_double * 2)()
+    """(phi kernel, composition kernel, mass correction) milliseconds summed over nsteps."""
+    ms = (ctypes.c_double * 3)()
     _check(load().lbpf_step_timed(ctx, int(nsteps), ms), ctx)
-    return float(ms[0]), float(ms[1])
+    return float(ms[0]), float(ms[1]), float(ms[2])
+
+
+def lbpf_solute_mass(ctx):
+    """(exact population mass, mass held by the correction or NaN)."""
+    m, t = ctypes.c_double(), ctypes.c_double()
+    _check(load().lbpf_solute_mass(ctx, ctypes.byref(m), ctypes.byref(t)), ctx)
+    return m.value, t.value
 
 
 def lbpf_mass(ctx):
@@ -192,7 +201,7 @@ def lbpf_lattice_info(lattice: int):
 
 # ---- convenience wrapper -------------------------------------------------------------
 
-def params_from(model, precision="fp64", dx=1.0, dt=1.0) -> lbpf_params:
+def params_from(model, precision="fp64", dx=1.0, dt=1.0, mass_every=0) -> lbpf_params:
     """lbpf_params from a workloads.ModelParams (lattice units unless dx, dt given)."""
     p = lbpf_default_params()
     p.nx, p.ny, p.nz = model.nx, model.ny, model.nz
@@ -206,6 +215,7 @@ def params_from(model, precision="fp64", dx=1.0, dt=1.0) -> lbpf_params:
     p.c_s_co, p.c_l_co, p.mu_eq = model.c_s_co, model.c_l_co, model.mu_eq
     p.counter_term, p.anti_trapping = int(model.counter_term), int(model.anti_trapping)
     p.a_at, p.eps_n = model.a_at, model.eps_n
+    p.mass_every = int(mass_every)
     return p
 
 
@@ -213,9 +223,9 @@ class Simulation:
     """One GPU simulation context.  Host fields in/out are numpy float64 arrays
     shaped (nz, ny, nx); device fields are CUDA float64 tensors."""
 
-    def __init__(self, model, phi0, c0, precision="fp64", stream=None, lattice=None):
+    def __init__(self, model, phi0, c0, precision="fp64", stream=None, lattice=None, mass_every=0):
         self.model = model
-        self.params = params_from(model, precision)
+        self.params = params_from(model, precision, mass_every=mass_every)
         if lattice is not None:
             self.params.lattice = int(lattice)
         is_dev = hasattr(phi0, "data_ptr")
@@ -235,6 +245,9 @@ class Simulation:
 
     def mass(self):
         return lbpf_mass(self.ctx)
+
+    def solute_mass(self):
+        return lbpf_solute_mass(self.ctx)
 
     def fields(self):
         phi, c, mu = (np.empty(self.shape) for _ in range(3))
