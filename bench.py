@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=20, help="steps of the FP64 comparison run")
+    ap.add_argument("--batch-steps", type=int, default=40,
+                    help="timed steps of the 384-instance 2-D batch (0 = skip)")
     return ap.parse_args()
 
 
@@ -144,6 +146,35 @@ def algorithmic_bytes(q: int, real: int, store: int):
     phi_kernel = 2 * q * store + 2 * real
     c_kernel = 2 * q * store
     return phi_kernel, c_kernel
+
+
+def batch_measurement(args, stream, hbm):
+    """The 384-instance 2-D sweep (sizes 64..768, 1-8 discs, random D_l and
+    M_phi/D_l, counter term on or off), FP32, stepped as one batch: one
+    persistent launch per kernel phase, two steps per replayed CUDA graph."""
+    import torch
+    from paper_2111_05960_gb300 import lbpf as L
+    from paper_2111_05960_gb300 import workloads as WL
+    inst = WL.batch_2d(count=384, seed=1)
+    b = L.BatchSimulation([x.params for x in inst], [x.phi for x in inst], [x.c for x in inst],
+                          precision="fp32", stream=stream.cuda_stream)
+    nodes = b.nodes
+    b.step(6)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(args.batch_steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.batch_steps
+    k_phi, k_c, _ = b.step_timed(10)
+    b.close()
+    bytes_node = 2 * 9 * 4 + 2 * 4 + 2 * 9 * 4     # phi kernel 80 B, composition kernel 72 B
+    gbs = bytes_node * nodes / (ms * 1e-3) / 1e9
+    return {"workload": "batch_2d_384_d2q9_fp32", "instances": 384, "nodes": nodes, "steps": args.batch_steps,
+            "ms_per_step": ms, "mlups": nodes / (ms * 1e-3) / 1e6, "bytes_per_node": bytes_node,
+            "achieved_gbs": gbs, "frac": gbs / hbm, "launch": "2 persistent launches per step, CUDA graph",
+            "kernel_ms": {"k_batch_phi": k_phi / 10, "k_batch_c": k_c / 10}}
 
 
 def cpu_baseline(model, phi0, c0, budget_s=12.0):
@@ -287,6 +318,13 @@ def run_ours(args):
         extra["fp64_forward"] = {"ms_per_step": ms64, "mlups": N / (ms64 * 1e-3) / 1e6,
                                  "fp32_speedup": ms64 / ms_per_step}
 
+    batch = None
+    if args.batch_steps > 0 and prec == "fp32":
+        try:
+            batch = batch_measurement(args, stream, hbm)
+        except Exception as ex:   # reported, never silently dropped
+            batch = {"error": str(ex)}
+
     e2e = None
     if not args.no_e2e:
         # end to end through the public API with host buffers: create from pinned host
@@ -335,7 +373,7 @@ def run_ours(args):
                           "parallelism": "replicas" if world > 1 else "single GPU",
                           "l2": "state %.1f GB per buffer set, larger than L2 (no flush needed)"
                                 % (N * (2 * q * store + 2 * real) / 1e9)},
-               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "batch_2d": batch,
                "gpu_launches": (4 if mass_every else 2) * args.steps, "clocks": clk,
                "mass": {"solute_before": m_before, "solute_after": m_after,
                         "relative_drift": (m_after - m_before) / m_before,

@@ -30,7 +30,10 @@
  *     context owns its populations, fields and scratch; lbpf_destroy frees them.
  *   - Work is queued on the CUDA stream given at creation (NULL = legacy default
  *     stream).  lbpf_step returns once the kernels are queued; lbpf_mass,
- *     lbpf_get_fields and lbpf_get_populations synchronise that stream.
+ *     lbpf_get_fields and lbpf_get_populations synchronise that stream.  On a
+ *     non-default stream, lbpf_step replays two steps captured once as a CUDA
+ *     graph (when every step has the same kernels: mass_every <= 1); the first
+ *     call that captures must not itself run inside another capture.
  *   - One context must not be used by two threads at once.
  *   - After LBPF_EUNSTABLE or LBPF_ETIMEOUT the context is poisoned: every later
  *     call except lbpf_last_error and lbpf_destroy returns LBPF_ESTATE.
@@ -171,6 +174,30 @@ lbpf_status lbpf_step_timed(lbpf_ctx *ctx, int64_t nsteps, double *kernel_ms);
  * (1,0),(0,1),(-1,0),(0,-1), e5..e8 diagonals (1,1),(-1,1),(-1,-1),(1,-1)).
  * Needs no GPU.  Errors: EINVAL for an unknown lattice or q == NULL. */
 lbpf_status lbpf_lattice_info(int32_t lattice, int32_t *q, int32_t *e, double *w);
+
+/* Batch of 2-D instances of uneven size in one context (a parameter sweep,
+ * counter term on and off, ...), stepped together: each kernel phase is one
+ * persistent launch over a flat list of 32 x 8 tiles of all instances, so the
+ * work is balanced whatever the size mix.  p[i], phi0[i], c0[i] describe
+ * instance i exactly as for lbpf_create (each with its own sizes, walls and
+ * parameters); all instances must be D2Q9 with the same precision and
+ * mass_every = 0.  The fields are copied; ptr_is_device says where phi0[i] and
+ * c0[i] live.  lbpf_step, lbpf_step_timed and lbpf_mass (sums over all
+ * instances) work on a batch; lbpf_get_fields, lbpf_get_populations and
+ * lbpf_solute_mass return LBPF_EUNSUPPORTED (use the calls below).
+ * Errors: EINVAL (NULL pointers, n < 1, an invalid instance: the message names
+ * it), EUNSUPPORTED (non-D2Q9 instance, mass_every != 0), ENOMEM, ECUDA. */
+lbpf_status lbpf_create_batch(const lbpf_params *p, int32_t n, const double *const *phi0,
+                              const double *const *c0, int32_t ptr_is_device, void *cuda_stream,
+                              lbpf_ctx **out);
+
+/* Fields of instance i of a batch, as lbpf_get_fields (FP64 [ny][nx]). */
+lbpf_status lbpf_batch_get_fields(lbpf_ctx *ctx, int32_t i, double *phi, double *c, double *mu,
+                                  int32_t ptr_is_device);
+
+/* Exact solute mass of every instance of a batch, as lbpf_solute_mass:
+ * masses[i] for i < n (host memory).  Synchronises. */
+lbpf_status lbpf_batch_solute_mass(lbpf_ctx *ctx, double *masses);
 
 /* Largest n that lbpf_mass_noalloc accepts: 4096 blocks x 16384 elements. */
 #define LBPF_NOALLOC_MAX_ELEMENTS 67108864LL

@@ -15,6 +15,7 @@
 
 #include "lbpf.h"
 #include "step_kernels.cuh"
+#include "batch_kernels.cuh"
 
 using namespace lbpf;
 
@@ -23,6 +24,7 @@ namespace {
 thread_local std::string g_thread_error;
 
 struct Dispatch;
+struct BatchDispatch;
 
 }  // namespace
 
@@ -53,6 +55,18 @@ struct lbpf_ctx {
     bool poisoned = false;
     std::string err;
     const Dispatch* ops = nullptr;
+    // a batch of 2-D instances (lbpf_create_batch)
+    bool is_batch = false;
+    int nb = 0;
+    std::vector<BatchInst> binst;      // host copy of the instance table
+    BatchInst* d_binst = nullptr;
+    int* d_tile_inst = nullptr;
+    int ntiles = 0;
+    int persist_blocks = 0;
+    const BatchDispatch* bops = nullptr;
+    // two steps captured as a CUDA graph (replayed by lbpf_step)
+    cudaGraphExec_t graph = nullptr;
+    bool graph_failed = false;
 };
 
 namespace {
@@ -81,7 +95,7 @@ struct Dispatch {
     void (*launch_c)(lbpf_ctx*, int cur, double* mass_partials);
     void (*launch_init)(lbpf_ctx*);
     void (*launch_pops_out)(lbpf_ctx*, double* g, double* h);
-    void (*launch_corr)(lbpf_ctx*, int cur_after, long long offset);
+    void (*launch_corr)(lbpf_ctx*, int cur_after);
     void (*launch_pop_mass)(lbpf_ctx*);
     int (*c_blocks)(const lbpf_ctx*);
 };
@@ -177,12 +191,11 @@ struct Impl {
             (const S*)ctx->h[cur], g, h);
     }
     // mass correction after a composition step whose new state has parity `cur_after`
-    static void launch_corr(lbpf_ctx* ctx, int cur_after, long long offset) {
+    static void launch_corr(lbpf_ctx* ctx, int cur_after) {
         k_mass_corr_plan<<<1, kMassThreads, 0, ctx->stream>>>(ctx->corr_partials, ctx->corr_blocks, ctx->corr,
                                                              ctx->sp.N, kCorrDelta);
         k_mass_corr_apply<SP><<<64, 256, 0, ctx->stream>>>(ctx->corr, (R*)ctx->c[cur_after],
-                                                           (S*)ctx->h[cur_after], ctx->sp.N, offset,
-                                                           ctx->corr_stride);
+                                                           (S*)ctx->h[cur_after], ctx->sp.N, ctx->corr_stride);
     }
     static void launch_pop_mass(lbpf_ctx* ctx) {
         k_pop_mass<L, SP><<<ctx->mass_blocks, kMassThreads, 0, ctx->stream>>>(
@@ -216,6 +229,89 @@ const Dispatch* pick(int lattice, int precision) {
             case LBPF_FP32_BF16DEV: return Impl<D3Q19, StoreBF16Dev>::table();
             case LBPF_FP32_FP16DEV: return Impl<D3Q19, StoreF16Dev>::table();
         }
+    }
+    return nullptr;
+}
+
+// ---- batch of 2-D instances -------------------------------------------------------
+
+struct BatchDispatch {
+    lbpf_status (*prepare)(lbpf_ctx*);
+    void (*launch_phi)(lbpf_ctx*, int cur);
+    void (*launch_c)(lbpf_ctx*, int cur);
+    void (*launch_init)(lbpf_ctx*, int i);
+    void (*fields_out)(lbpf_ctx*, int i, double* phi, double* c, double* mu);
+    void (*pop_mass)(lbpf_ctx*, int i);   // exact mass of instance i into mass_out[0]
+};
+
+template <class SP>
+struct BatchImpl {
+    using R = typename SP::real;
+    using S = typename SP::store_t;
+    static constexpr size_t smem_phi = batch_smem<SP>(true);
+    static constexpr size_t smem_c = batch_smem<SP>(false);
+
+    static lbpf_status prepare(lbpf_ctx* ctx) {
+        LBPF_CUDA(ctx, cudaFuncSetAttribute(k_batch_step<SP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem_phi));
+        LBPF_CUDA(ctx, cudaFuncSetAttribute(k_batch_step<SP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem_c));
+        int sms = 0, occ_phi = 0, occ_c = 0;
+        LBPF_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+        LBPF_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_phi, k_batch_step<SP, true>,
+                                                                     32 * kBatchBY, smem_phi));
+        LBPF_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_c, k_batch_step<SP, false>,
+                                                                     32 * kBatchBY, smem_c));
+        const int occ = std::max(1, std::min(occ_phi, occ_c));
+        ctx->persist_blocks = std::max(1, std::min(ctx->ntiles, sms * occ));
+        return LBPF_OK;
+    }
+    static void launch_phi(lbpf_ctx* ctx, int cur) {
+        const int nxt = cur ^ 1;
+        k_batch_step<SP, true><<<ctx->persist_blocks, dim3(32, kBatchBY), smem_phi, ctx->stream>>>(
+            ctx->d_binst, ctx->d_tile_inst, ctx->ntiles, (const S*)ctx->g[cur], (S*)ctx->g[nxt],
+            (const R*)ctx->phi[cur], nullptr, (const R*)ctx->c[cur], (R*)ctx->phi[nxt]);
+    }
+    static void launch_c(lbpf_ctx* ctx, int cur) {
+        const int nxt = cur ^ 1;
+        k_batch_step<SP, false><<<ctx->persist_blocks, dim3(32, kBatchBY), smem_c, ctx->stream>>>(
+            ctx->d_binst, ctx->d_tile_inst, ctx->ntiles, (const S*)ctx->h[cur], (S*)ctx->h[nxt],
+            (const R*)ctx->phi[cur], (const R*)ctx->phi[nxt], (const R*)ctx->c[cur], (R*)ctx->c[nxt]);
+    }
+    static void launch_init(lbpf_ctx* ctx, int i) {
+        const BatchInst& I = ctx->binst[i];
+        const int cur = ctx->cur;
+        k_init<D2Q9, SP><<<(unsigned)((I.K.P.N + 255) / 256), 256, 0, ctx->stream>>>(
+            I.K, (const R*)ctx->phi[cur] + I.fld_off, (R*)ctx->c[cur] + I.fld_off, (S*)ctx->g[cur] + I.pop_off,
+            (S*)ctx->h[cur] + I.pop_off);
+    }
+    static void fields_out(lbpf_ctx* ctx, int i, double* ophi, double* oc, double* omu) {
+        const BatchInst& I = ctx->binst[i];
+        const int cur = ctx->cur;
+        k_fields_out<R><<<(unsigned)((I.K.P.N + 255) / 256), 256, 0, ctx->stream>>>(
+            I.K, (const R*)ctx->phi[cur] + I.fld_off, (const R*)ctx->c[cur] + I.fld_off, ophi, oc, omu);
+    }
+    static void pop_mass(lbpf_ctx* ctx, int i) {
+        const BatchInst& I = ctx->binst[i];
+        const int cur = ctx->cur;
+        const int blocks = (int)std::min<long long>((I.K.P.N + kMassThreads - 1) / kMassThreads, ctx->mass_blocks);
+        k_pop_mass<D2Q9, SP><<<blocks, kMassThreads, 0, ctx->stream>>>(
+            I.K, (const R*)ctx->phi[cur] + I.fld_off, (const R*)ctx->c[cur] + I.fld_off,
+            (const S*)ctx->h[cur] + I.pop_off, ctx->partials);
+        k_mass_final<<<1, kMassThreads, 0, ctx->stream>>>(ctx->partials, blocks, ctx->mass_out);
+    }
+    static const BatchDispatch* table() {
+        static const BatchDispatch d = {prepare, launch_phi, launch_c, launch_init, fields_out, pop_mass};
+        return &d;
+    }
+};
+
+const BatchDispatch* pick_batch(int precision) {
+    switch (precision) {
+        case LBPF_FP64: return BatchImpl<StoreF64>::table();
+        case LBPF_FP32: return BatchImpl<StoreF32>::table();
+        case LBPF_FP32_BF16DEV: return BatchImpl<StoreBF16Dev>::table();
+        case LBPF_FP32_FP16DEV: return BatchImpl<StoreF16Dev>::table();
     }
     return nullptr;
 }
@@ -270,6 +366,26 @@ StepParams lattice_units(const lbpf_params* p) {
     return s;
 }
 
+// Geometry, coefficients (FP64 and FP32) and link offsets of one simulation.
+KParams make_kparams(const lbpf_params* p) {
+    KParams kp;
+    kp.P = lattice_units(p);
+    kp.cd = make_coef<double>(kp.P);
+    kp.cf = make_coef<float>(kp.P);
+    const int q = p->lattice == LBPF_D3Q19 ? 19 : 9;
+    for (int k = 0; k < 19; ++k) {
+        int e[3] = {0, 0, 0};
+        if (k < q) {
+            if (p->lattice == LBPF_D3Q19) { e[0] = D3Q19::ex(k); e[1] = D3Q19::ey(k); e[2] = D3Q19::ez(k); }
+            else { e[0] = D2Q9::ex(k); e[1] = D2Q9::ey(k); }
+        }
+        const long long nx = p->nx, nxy = (long long)p->nx * p->ny;
+        kp.kN[k] = (long long)k * kp.P.N;
+        kp.koff[k] = kp.kN[k] - (e[0] + e[1] * nx + e[2] * nxy);
+    }
+    return kp;
+}
+
 void free_all(lbpf_ctx* ctx) {
     for (int i = 0; i < 2; ++i) {
         cudaFree(ctx->g[i]); cudaFree(ctx->h[i]); cudaFree(ctx->phi[i]); cudaFree(ctx->c[i]);
@@ -280,16 +396,72 @@ void free_all(lbpf_ctx* ctx) {
     cudaFree(ctx->corr_partials); cudaFree(ctx->corr);
     ctx->corr_partials = nullptr;
     ctx->corr = nullptr;
+    cudaFree(ctx->d_binst); cudaFree(ctx->d_tile_inst);
+    ctx->d_binst = nullptr;
+    ctx->d_tile_inst = nullptr;
+    if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
 }
 
 // One coupled step (both kernels), followed by the mass correction when it is due.
 void launch_one_step(lbpf_ctx* ctx) {
+    if (ctx->is_batch) {
+        ctx->bops->launch_phi(ctx, ctx->cur);
+        ctx->bops->launch_c(ctx, ctx->cur);
+        ctx->cur ^= 1;
+        ctx->step += 1;
+        return;
+    }
     const bool corr = ctx->corr && ((ctx->step + 1) % ctx->p.mass_every == 0);
     ctx->ops->launch_phi(ctx, ctx->cur);
     ctx->ops->launch_c(ctx, ctx->cur, corr ? ctx->corr_partials : nullptr);
-    if (corr) ctx->ops->launch_corr(ctx, ctx->cur ^ 1, (long long)((ctx->step * 7919LL) % ctx->sp.N));
+    if (corr) ctx->ops->launch_corr(ctx, ctx->cur ^ 1);
     ctx->cur ^= 1;
     ctx->step += 1;
+}
+
+lbpf_status check_launch(lbpf_ctx* ctx, const char* what);
+
+// nsteps steps, replaying two-step CUDA graphs where possible: on a non-default
+// stream, when every step has the same kernels (mass correction off or every
+// step).  The graph is captured once per context; if capture fails the steps
+// are launched one by one.
+lbpf_status run_steps(lbpf_ctx* ctx, int64_t nsteps) {
+    const bool graphable = ctx->stream != nullptr && !ctx->graph_failed &&
+                           (ctx->p.mass_every <= 1 || ctx->is_batch) && nsteps >= 4;
+    if (!graphable) {
+        for (int64_t s = 0; s < nsteps; ++s) launch_one_step(ctx);
+        return check_launch(ctx, "step kernels");
+    }
+    if (ctx->cur == 1) { launch_one_step(ctx); --nsteps; }   // graphs start from parity 0
+    if (!ctx->graph) {
+        cudaGraph_t g = nullptr;
+        const int64_t step0 = ctx->step;
+        cudaError_t e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            launch_one_step(ctx);
+            launch_one_step(ctx);
+            e = cudaStreamEndCapture(ctx->stream, &g);
+        }
+        ctx->step = step0;          // capture only recorded the launches
+        ctx->cur = 0;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->graph, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            ctx->graph = nullptr;
+            ctx->graph_failed = true;
+            for (int64_t s = 0; s < nsteps; ++s) launch_one_step(ctx);
+            return check_launch(ctx, "step kernels");
+        }
+    }
+    for (; nsteps >= 2; nsteps -= 2) {
+        cudaError_t e = cudaGraphLaunch(ctx->graph, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphLaunch");
+        ctx->step += 2;
+    }
+    if (nsteps == 1) launch_one_step(ctx);
+    return check_launch(ctx, "step kernels");
 }
 
 // A prime stride coprime with N for spreading the corrected nodes.
@@ -382,19 +554,7 @@ lbpf_status lbpf_create(const lbpf_params* p, const double* phi0, const double* 
     ctx->p = *p;
     ctx->sp = lattice_units(p);
     ctx->q = p->lattice == LBPF_D3Q19 ? 19 : 9;
-    ctx->kp.P = ctx->sp;
-    ctx->kp.cd = make_coef<double>(ctx->sp);
-    ctx->kp.cf = make_coef<float>(ctx->sp);
-    for (int k = 0; k < 19; ++k) {
-        int e[3] = {0, 0, 0};
-        if (k < ctx->q) {
-            if (p->lattice == LBPF_D3Q19) { e[0] = D3Q19::ex(k); e[1] = D3Q19::ey(k); e[2] = D3Q19::ez(k); }
-            else { e[0] = D2Q9::ex(k); e[1] = D2Q9::ey(k); }
-        }
-        const long long nx = p->nx, nxy = (long long)p->nx * p->ny;
-        ctx->kp.kN[k] = (long long)k * ctx->sp.N;
-        ctx->kp.koff[k] = ctx->kp.kN[k] - (e[0] + e[1] * nx + e[2] * nxy);
-    }
+    ctx->kp = make_kparams(p);
     ctx->ops = ops;
     ctx->stream = (cudaStream_t)cuda_stream;
     ctx->real_size = p->precision == LBPF_FP64 ? 8 : 4;
@@ -472,8 +632,7 @@ lbpf_status lbpf_step(lbpf_ctx* ctx, int64_t nsteps) {
     if (!ctx) return fail(nullptr, LBPF_EINVAL, "ctx is NULL");
     if (ctx->poisoned) return fail(ctx, LBPF_ESTATE, "context poisoned by an earlier error");
     if (nsteps < 0) return fail(ctx, LBPF_EINVAL, "nsteps < 0");
-    for (int64_t s = 0; s < nsteps; ++s) launch_one_step(ctx);
-    return check_launch(ctx, "step kernels");
+    return run_steps(ctx, nsteps);
 }
 
 lbpf_status lbpf_step_timed(lbpf_ctx* ctx, int64_t nsteps, double* kernel_ms) {
@@ -492,11 +651,13 @@ lbpf_status lbpf_step_timed(lbpf_ctx* ctx, int64_t nsteps, double* kernel_ms) {
         for (int64_t s = 0; s < nsteps; ++s) {
             const bool corr = ctx->corr && ((ctx->step + 1) % ctx->p.mass_every == 0);
             cudaEventRecord(ev[4 * s], ctx->stream);
-            ctx->ops->launch_phi(ctx, ctx->cur);
+            if (ctx->is_batch) ctx->bops->launch_phi(ctx, ctx->cur);
+            else ctx->ops->launch_phi(ctx, ctx->cur);
             cudaEventRecord(ev[4 * s + 1], ctx->stream);
-            ctx->ops->launch_c(ctx, ctx->cur, corr ? ctx->corr_partials : nullptr);
+            if (ctx->is_batch) ctx->bops->launch_c(ctx, ctx->cur);
+            else ctx->ops->launch_c(ctx, ctx->cur, corr ? ctx->corr_partials : nullptr);
             cudaEventRecord(ev[4 * s + 2], ctx->stream);
-            if (corr) ctx->ops->launch_corr(ctx, ctx->cur ^ 1, (long long)((ctx->step * 7919LL) % ctx->sp.N));
+            if (corr) ctx->ops->launch_corr(ctx, ctx->cur ^ 1);
             cudaEventRecord(ev[4 * s + 3], ctx->stream);
             ctx->cur ^= 1;
             ctx->step += 1;
@@ -541,6 +702,7 @@ lbpf_status lbpf_mass(lbpf_ctx* ctx, double* total_c, double* total_phi) {
 
 lbpf_status lbpf_solute_mass(lbpf_ctx* ctx, double* mass, double* target) {
     if (!ctx || !mass) return fail(ctx, LBPF_EINVAL, "NULL argument");
+    if (ctx->is_batch) return fail(ctx, LBPF_EUNSUPPORTED, "a batch context: use the lbpf_batch_* calls");
     if (ctx->poisoned) return fail(ctx, LBPF_ESTATE, "context poisoned by an earlier error");
     ctx->ops->launch_pop_mass(ctx);
     lbpf_status st = check_launch(ctx, "population mass kernels");
@@ -558,6 +720,7 @@ lbpf_status lbpf_solute_mass(lbpf_ctx* ctx, double* mass, double* target) {
 
 lbpf_status lbpf_get_fields(lbpf_ctx* ctx, double* phi, double* c, double* mu, int32_t ptr_is_device) {
     if (!ctx) return fail(nullptr, LBPF_EINVAL, "ctx is NULL");
+    if (ctx->is_batch) return fail(ctx, LBPF_EUNSUPPORTED, "a batch context: use the lbpf_batch_* calls");
     if (ctx->poisoned) return fail(ctx, LBPF_ESTATE, "context poisoned by an earlier error");
     const size_t N = (size_t)ctx->sp.N;
     double *dphi = phi, *dc = c, *dmu = mu;
@@ -583,6 +746,7 @@ lbpf_status lbpf_get_fields(lbpf_ctx* ctx, double* phi, double* c, double* mu, i
 
 lbpf_status lbpf_get_populations(lbpf_ctx* ctx, double* g, double* h, int32_t ptr_is_device) {
     if (!ctx) return fail(nullptr, LBPF_EINVAL, "ctx is NULL");
+    if (ctx->is_batch) return fail(ctx, LBPF_EUNSUPPORTED, "a batch context: use the lbpf_batch_* calls");
     if (ctx->poisoned) return fail(ctx, LBPF_ESTATE, "context poisoned by an earlier error");
     const size_t bytes = sizeof(double) * ctx->q * (size_t)ctx->sp.N;
     double *dg = g, *dh = h, *tmp = nullptr;
@@ -603,6 +767,163 @@ lbpf_status lbpf_get_populations(lbpf_ctx* ctx, double* g, double* h, int32_t pt
     if (tmp) cudaFree(tmp);
     if (st == LBPF_OK && e != cudaSuccess) st = cuda_fail(ctx, e, "population export");
     return st;
+}
+
+lbpf_status lbpf_create_batch(const lbpf_params* p, int32_t n, const double* const* phi0,
+                              const double* const* c0, int32_t ptr_is_device, void* cuda_stream, lbpf_ctx** out) {
+    if (!out) return fail(nullptr, LBPF_EINVAL, "out pointer is NULL");
+    *out = nullptr;
+    if (!p || !phi0 || !c0 || n < 1) return fail(nullptr, LBPF_EINVAL, "NULL argument or n < 1");
+    for (int i = 0; i < n; ++i) {
+        std::string why;
+        if (!phi0[i] || !c0[i]) return fail(nullptr, LBPF_EINVAL, "NULL field pointer of instance " + std::to_string(i));
+        if (validate(&p[i], why) != LBPF_OK) return fail(nullptr, LBPF_EINVAL, "instance " + std::to_string(i) + ": " + why);
+        if (p[i].lattice != LBPF_D2Q9) return fail(nullptr, LBPF_EUNSUPPORTED, "batches hold 2-D D2Q9 instances");
+        if (p[i].precision != p[0].precision) return fail(nullptr, LBPF_EINVAL, "all instances need one precision");
+        if (p[i].mass_every != 0) return fail(nullptr, LBPF_EUNSUPPORTED, "mass correction is not built for batches");
+    }
+    const BatchDispatch* bops = pick_batch(p[0].precision);
+    if (!bops) return fail(nullptr, LBPF_EUNSUPPORTED, "precision not built");
+    lbpf_ctx* ctx = new (std::nothrow) lbpf_ctx();
+    if (!ctx) return fail(nullptr, LBPF_ENOMEM, "host allocation failed");
+    ctx->is_batch = true;
+    ctx->nb = n;
+    ctx->bops = bops;
+    ctx->p = p[0];
+    ctx->q = 9;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    ctx->real_size = p[0].precision == LBPF_FP64 ? 8 : 4;
+    ctx->store_size = p[0].precision == LBPF_FP64 ? 8 : (p[0].precision == LBPF_FP32 ? 4 : 2);
+    auto abort_create = [&](lbpf_status st) {
+        std::string m = ctx->err;
+        free_all(ctx);
+        delete ctx;
+        g_thread_error = m;
+        return st;
+    };
+    // instance table: offsets into the concatenated buffers and the flat tile list
+    long long nodes = 0;
+    int tiles = 0;
+    std::vector<int> tile_inst;
+    try {
+        ctx->binst.resize(n);
+        for (int i = 0; i < n; ++i) {
+            BatchInst& I = ctx->binst[i];
+            I.K = make_kparams(&p[i]);
+            I.fld_off = nodes;
+            I.pop_off = 9 * nodes;
+            I.tiles_x = (p[i].nx + 31) / 32;
+            const int ty = (p[i].ny + kBatchBY - 1) / kBatchBY;
+            I.tile_begin = tiles;
+            I.walls = (p[i].bc[0] || p[i].bc[1]) ? 1 : 0;
+            I.pad = 0;
+            for (int t = 0; t < I.tiles_x * ty; ++t) tile_inst.push_back(i);
+            tiles += I.tiles_x * ty;
+            nodes += I.K.P.N;
+        }
+    } catch (...) {
+        return abort_create(fail(ctx, LBPF_ENOMEM, "host allocation failed"));
+    }
+    ctx->ntiles = tiles;
+    // the whole batch as one field of `nodes` values, for lbpf_mass
+    ctx->sp = ctx->binst[0].K.P;
+    ctx->sp.N = nodes;
+    ctx->sp.nx = (int)std::min<long long>(nodes, 1LL << 30);
+    ctx->kp = ctx->binst[0].K;
+    lbpf_status st;
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e != cudaSuccess) { cuda_fail(ctx, e, "cudaGetDevice"); return abort_create(LBPF_ECUDA); }
+    const size_t N = (size_t)nodes;
+    for (int i = 0; i < 2; ++i) {
+        if ((st = alloc(ctx, &ctx->g[i], ctx->store_size * 9 * N, "g populations")) != LBPF_OK) return abort_create(st);
+        if ((st = alloc(ctx, &ctx->h[i], ctx->store_size * 9 * N, "h populations")) != LBPF_OK) return abort_create(st);
+        if ((st = alloc(ctx, &ctx->phi[i], ctx->real_size * N, "phi field")) != LBPF_OK) return abort_create(st);
+        if ((st = alloc(ctx, &ctx->c[i], ctx->real_size * N, "c field")) != LBPF_OK) return abort_create(st);
+    }
+    if ((st = alloc(ctx, (void**)&ctx->d_binst, sizeof(BatchInst) * n, "instance table")) != LBPF_OK) return abort_create(st);
+    if ((st = alloc(ctx, (void**)&ctx->d_tile_inst, sizeof(int) * tiles, "tile list")) != LBPF_OK) return abort_create(st);
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    ctx->mass_blocks = (int)std::max<long long>(1, std::min<long long>((nodes + kMassThreads - 1) / kMassThreads, 4LL * sms));
+    if ((st = alloc(ctx, (void**)&ctx->partials, sizeof(double) * 3 * ctx->mass_blocks, "mass partials")) != LBPF_OK) return abort_create(st);
+    if ((st = alloc(ctx, (void**)&ctx->mass_out, sizeof(double) * 3, "mass result")) != LBPF_OK) return abort_create(st);
+    e = cudaMemcpyAsync(ctx->d_binst, ctx->binst.data(), sizeof(BatchInst) * n, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->d_tile_inst, tile_inst.data(), sizeof(int) * tiles, cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) { cuda_fail(ctx, e, "instance table"); return abort_create(LBPF_ECUDA); }
+    if ((st = bops->prepare(ctx)) != LBPF_OK) return abort_create(st);
+    // fields: per instance into the staging buffer (host) or straight from the caller (device)
+    if (!ptr_is_device) {
+        if ((st = ensure_staging(ctx)) != LBPF_OK) return abort_create(st);
+    }
+    for (int i = 0; i < n; ++i) {
+        const BatchInst& I = ctx->binst[i];
+        const size_t Ni = (size_t)I.K.P.N;
+        const double* sphi = phi0[i];
+        const double* sc = c0[i];
+        if (!ptr_is_device) {
+            e = cudaMemcpyAsync(ctx->staging + I.fld_off, phi0[i], sizeof(double) * Ni, cudaMemcpyHostToDevice, ctx->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(ctx->staging + N + I.fld_off, c0[i], sizeof(double) * Ni, cudaMemcpyHostToDevice, ctx->stream);
+            if (e != cudaSuccess) { cuda_fail(ctx, e, "copy of phi0/c0"); return abort_create(LBPF_ECUDA); }
+            sphi = ctx->staging + I.fld_off;
+            sc = ctx->staging + N + I.fld_off;
+        }
+        if (is_f64(ctx)) {
+            launch_from_f64<double>(sphi, (double*)ctx->phi[0] + I.fld_off, (long long)Ni, ctx->stream);
+            launch_from_f64<double>(sc, (double*)ctx->c[0] + I.fld_off, (long long)Ni, ctx->stream);
+        } else {
+            launch_from_f64<float>(sphi, (float*)ctx->phi[0] + I.fld_off, (long long)Ni, ctx->stream);
+            launch_from_f64<float>(sc, (float*)ctx->c[0] + I.fld_off, (long long)Ni, ctx->stream);
+        }
+    }
+    ctx->cur = 0;
+    for (int i = 0; i < n; ++i) bops->launch_init(ctx, i);
+    if ((st = check_launch(ctx, "initialisation kernels")) != LBPF_OK) return abort_create(st);
+    e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) { cuda_fail(ctx, e, "initialisation"); return abort_create(LBPF_ECUDA); }
+    *out = ctx;
+    return LBPF_OK;
+}
+
+lbpf_status lbpf_batch_get_fields(lbpf_ctx* ctx, int32_t i, double* phi, double* c, double* mu, int32_t ptr_is_device) {
+    if (!ctx) return fail(nullptr, LBPF_EINVAL, "ctx is NULL");
+    if (!ctx->is_batch) return fail(ctx, LBPF_EINVAL, "not a batch context");
+    if (ctx->poisoned) return fail(ctx, LBPF_ESTATE, "context poisoned by an earlier error");
+    if (i < 0 || i >= ctx->nb) return fail(ctx, LBPF_EINVAL, "instance index out of range");
+    const size_t Ni = (size_t)ctx->binst[i].K.P.N;
+    double *dphi = phi, *dc = c, *dmu = mu;
+    if (!ptr_is_device) {
+        lbpf_status st = ensure_staging(ctx);
+        if (st != LBPF_OK) return st;
+        dphi = phi ? ctx->staging : nullptr;
+        dc = c ? ctx->staging + Ni : nullptr;
+        dmu = mu ? ctx->staging + 2 * Ni : nullptr;
+    }
+    ctx->bops->fields_out(ctx, i, dphi, dc, dmu);
+    lbpf_status st = check_launch(ctx, "field export kernel");
+    if (st != LBPF_OK) return st;
+    if (!ptr_is_device) {
+        if (phi) LBPF_CUDA(ctx, cudaMemcpyAsync(phi, dphi, sizeof(double) * Ni, cudaMemcpyDeviceToHost, ctx->stream));
+        if (c) LBPF_CUDA(ctx, cudaMemcpyAsync(c, dc, sizeof(double) * Ni, cudaMemcpyDeviceToHost, ctx->stream));
+        if (mu) LBPF_CUDA(ctx, cudaMemcpyAsync(mu, dmu, sizeof(double) * Ni, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    LBPF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return LBPF_OK;
+}
+
+lbpf_status lbpf_batch_solute_mass(lbpf_ctx* ctx, double* masses) {
+    if (!ctx || !masses) return fail(ctx, LBPF_EINVAL, "NULL argument");
+    if (!ctx->is_batch) return fail(ctx, LBPF_EINVAL, "not a batch context");
+    if (ctx->poisoned) return fail(ctx, LBPF_ESTATE, "context poisoned by an earlier error");
+    for (int i = 0; i < ctx->nb; ++i) {
+        ctx->bops->pop_mass(ctx, i);
+        lbpf_status st = check_launch(ctx, "population mass kernels");
+        if (st != LBPF_OK) return st;
+        LBPF_CUDA(ctx, cudaMemcpyAsync(&masses[i], ctx->mass_out, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    LBPF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return LBPF_OK;
 }
 
 lbpf_status lbpf_get_step(const lbpf_ctx* ctx, int64_t* step) {

@@ -570,7 +570,7 @@ __device__ __forceinline__ void pull_combine(const KParams& K, const Coef<typena
 // FP64 block sum of the threads' mass accumulators, written to
 // partials[linear block index] (all threads of the block must call it).
 template <int NT, typename R>
-__device__ __forceinline__ void block_mass_out(const MassAcc<R>& m, double* __restrict__ partials) {
+__device__ __forceinline__ void block_mass_out(const MassAcc<R>& m, double* __restrict__ partials, long long slot) {
     __shared__ double red[NT / 32];
     double v = (double)m.hi + (double)m.lo;
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -580,7 +580,7 @@ __device__ __forceinline__ void block_mass_out(const MassAcc<R>& m, double* __re
     if (tid == 0) {
         double t = 0.0;
         for (int w = 0; w < NT / 32; ++w) t += red[w];
-        partials[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = t;
+        partials[slot] = t;
     }
 }
 
@@ -594,7 +594,8 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
                                       const typename SP::real* __restrict__ phi_np1,
                                       const typename SP::real* __restrict__ c_n,
                                       typename SP::real* __restrict__ moment_out,
-                                      double* __restrict__ mass_partials) {
+                                      double* __restrict__ mass_partials, int x0, int y0, int z0,
+                                      long long mass_slot) {
     using R = typename SP::real;
     using G = Geo<L, BY>;
     const StepParams& P = K.P;
@@ -606,7 +607,6 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
     R* pst = cst + 2 * G::P1;                                        // [2][P1] phi^{n+1} (c kernel)
     R* sA = pst + (IS_PHI ? 0 : 2 * G::P1);                          // [NING][P1] (phi kernel)
 
-    const int x0 = blockIdx.x * G::BX, y0 = blockIdx.y * BY;
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     const bool active_xy = x < P.nx && y < P.ny;
     const bool inside2 = x0 >= 2 && x0 + G::BX + 2 <= P.nx && y0 >= 2 && y0 + BY + 2 <= P.ny;
@@ -640,14 +640,13 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
         if (active_xy)
             pull_combine<L, SP, BY, IS_PHI, WALLS>(K, C, fout, sing, sing, sing, sphi, sphi, sphi, sA, phi_np1,
                                                    moment_out, st, macc);
-        if (!IS_PHI && mass_partials) block_mass_out<G::NT>(macc, mass_partials);
+        if (!IS_PHI && mass_partials) block_mass_out<G::NT>(macc, mass_partials, mass_slot);
         return;
     }
 
     // z-march.  While plane z is pulled, the phi plane z+3 and the ring of z+2
     // stream into shared memory, and the loads of plane z overlap the
     // ingredients of z+1.  Stage buffers are indexed by zg & 1 (zg >= -1).
-    const int z0 = blockIdx.z * ZCH;
     const int z1 = min(z0 + ZCH, P.nz);
     auto fslot = [&](int zg) { return sphi + ((zg - z0 + 2 + 5 * ZCH) % 5) * G::P2; };
     auto islot = [&](int zg) { return (zg - z0 + 1 + 3 * ZCH) % 3; };
@@ -686,7 +685,7 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
                                                    phi_np1, moment_out, st, macc);
     }
     cp_async_wait_all();
-    if (!IS_PHI && mass_partials) block_mass_out<G::NT>(macc, mass_partials);
+    if (!IS_PHI && mass_partials) block_mass_out<G::NT>(macc, mass_partials, mass_slot);
 }
 
 template <class L, class SP, int BY, int ZCH>
@@ -704,7 +703,8 @@ __global__ void __launch_bounds__(32 * BY, MINB)
 k_phi_step(const KParams K, const typename SP::store_t* __restrict__ gin,
            typename SP::store_t* __restrict__ gout, const typename SP::real* __restrict__ phi_n,
            const typename SP::real* __restrict__ c_n, typename SP::real* __restrict__ phi_np1) {
-    march<L, SP, BY, ZCH, true, WALLS>(K, gin, gout, phi_n, nullptr, c_n, phi_np1, nullptr);
+    march<L, SP, BY, ZCH, true, WALLS>(K, gin, gout, phi_n, nullptr, c_n, phi_np1, nullptr,
+                                       blockIdx.x * 32, blockIdx.y * BY, blockIdx.z * ZCH, 0);
 }
 
 template <class L, class SP, int BY, int ZCH, int MINB, bool WALLS>
@@ -713,7 +713,9 @@ k_c_step(const KParams K, const typename SP::store_t* __restrict__ hin,
          typename SP::store_t* __restrict__ hout, const typename SP::real* __restrict__ phi_n,
          const typename SP::real* __restrict__ phi_np1, const typename SP::real* __restrict__ c_n,
          typename SP::real* __restrict__ c_np1, double* __restrict__ mass_partials) {
-    march<L, SP, BY, ZCH, false, WALLS>(K, hin, hout, phi_n, phi_np1, c_n, c_np1, mass_partials);
+    march<L, SP, BY, ZCH, false, WALLS>(K, hin, hout, phi_n, phi_np1, c_n, c_np1, mass_partials,
+                                        blockIdx.x * 32, blockIdx.y * BY, blockIdx.z * ZCH,
+                                        blockIdx.x + gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z));
 }
 
 // ---- initialisation -------------------------------------------------------------------
@@ -900,6 +902,7 @@ struct MassCorr {
     double measured;    // exact population mass after the last measured step
     double delta;       // increment per corrected node in the last correction
     long long count;    // nodes corrected by the last correction
+    unsigned long long round;  // corrections planned so far (rotates the node subset)
 };
 
 static __global__ void __launch_bounds__(kMassThreads)
@@ -918,17 +921,20 @@ k_mass_corr_plan(const double* __restrict__ partials, int nblocks, MassCorr* __r
         mc->measured = sc;
         mc->count = k;
         mc->delta = k > 0 ? dM / (double)k : 0.0;
+        mc->round += 1;
     }
 }
 
 // Node j of the correction is (offset + j * stride) mod N; stride is a large
-// prime, offset rotates with the step so that no node is corrected repeatedly.
+// prime coprime with N, and offset = 7919 * round mod N rotates with every
+// correction, so no node is corrected repeatedly.  Everything it needs is read
+// on the device, so the correction can be replayed from a captured graph.
 template <class SP>
 __global__ void k_mass_corr_apply(const MassCorr* __restrict__ mc, typename SP::real* __restrict__ c,
-                                  typename SP::store_t* __restrict__ h0, long long N, long long offset,
-                                  long long stride) {
+                                  typename SP::store_t* __restrict__ h0, long long N, long long stride) {
     using R = typename SP::real;
     const long long count = mc->count;
+    const long long offset = (long long)((mc->round * 7919ULL) % (unsigned long long)N);
     const R d = R(mc->delta);
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < count;
          j += (long long)gridDim.x * blockDim.x) {

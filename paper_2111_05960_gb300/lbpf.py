@@ -76,6 +76,10 @@ def load() -> ctypes.CDLL:
                               ctypes.POINTER(ctypes.c_int32), _dp],
         "lbpf_mass_noalloc": [_vp, _vp, ctypes.c_int64, ctypes.c_int32, _vp, _vp],
         "lbpf_solute_mass": [_vp, _dp, _dp],
+        "lbpf_create_batch": [ctypes.POINTER(lbpf_params), ctypes.c_int32, ctypes.POINTER(_vp),
+                              ctypes.POINTER(_vp), ctypes.c_int32, _vp, ctypes.POINTER(_vp)],
+        "lbpf_batch_get_fields": [_vp, ctypes.c_int32, _vp, _vp, _vp, ctypes.c_int32],
+        "lbpf_batch_solute_mass": [_vp, _dp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -91,7 +95,8 @@ def exported_symbols():
     """Names declared in include/lbpf.h that the loaded library must export."""
     return ["lbpf_default_params", "lbpf_create", "lbpf_step", "lbpf_step_timed", "lbpf_mass",
             "lbpf_get_fields", "lbpf_get_populations", "lbpf_get_step", "lbpf_destroy",
-            "lbpf_last_error", "lbpf_lattice_info", "lbpf_mass_noalloc", "lbpf_solute_mass"]
+            "lbpf_last_error", "lbpf_lattice_info", "lbpf_mass_noalloc", "lbpf_solute_mass",
+            "lbpf_create_batch", "lbpf_batch_get_fields", "lbpf_batch_solute_mass"]
 
 
 def _check(status: int, ctx=None):
@@ -176,6 +181,28 @@ def lbpf_destroy(ctx) -> None:
 def lbpf_last_error(ctx=None) -> str:
     m = load().lbpf_last_error(ctx)
     return m.decode() if m else ""
+
+
+def lbpf_create_batch(params, phi0s, c0s, ptr_is_device: int = 0, cuda_stream=None):
+    """params: sequence of lbpf_params; phi0s, c0s: sequences of per-instance fields."""
+    n = len(params)
+    arr = (lbpf_params * n)(*params)
+    pp = (_vp * n)(*[_ptr(a)[0] for a in phi0s])
+    cp = (_vp * n)(*[_ptr(a)[0] for a in c0s])
+    ctx = _vp()
+    _check(load().lbpf_create_batch(arr, n, pp, cp, int(ptr_is_device), cuda_stream or None, ctypes.byref(ctx)))
+    return ctx
+
+
+def lbpf_batch_get_fields(ctx, i: int, phi=None, c=None, mu=None, ptr_is_device: int = 0) -> None:
+    _check(load().lbpf_batch_get_fields(ctx, int(i), _ptr(phi)[0], _ptr(c)[0], _ptr(mu)[0],
+                                        int(ptr_is_device)), ctx)
+
+
+def lbpf_batch_solute_mass(ctx, n: int) -> np.ndarray:
+    out = np.zeros(n)
+    _check(load().lbpf_batch_solute_mass(ctx, out.ctypes.data_as(_dp)), ctx)
+    return out
 
 
 NOALLOC_MAX_ELEMENTS = 67108864
@@ -263,6 +290,47 @@ class Simulation:
     @property
     def t(self):
         return lbpf_get_step(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            lbpf_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchSimulation:
+    """Many 2-D instances stepped together (lbpf_create_batch).  models: sequence
+    of workloads.ModelParams; phis, cs: their initial fields."""
+
+    def __init__(self, models, phis, cs, precision="fp32", stream=None):
+        self.models = list(models)
+        self.n = len(self.models)
+        params = [params_from(m, precision) for m in self.models]
+        phis = [np.ascontiguousarray(a, dtype=np.float64) for a in phis]
+        cs = [np.ascontiguousarray(a, dtype=np.float64) for a in cs]
+        self.ctx = lbpf_create_batch(params, phis, cs, 0, stream)
+        self.nodes = sum(m.nodes for m in self.models)
+
+    def step(self, n=1):
+        lbpf_step(self.ctx, n)
+        return self
+
+    def step_timed(self, n):
+        return lbpf_step_timed(self.ctx, n)
+
+    def fields(self, i):
+        m = self.models[i]
+        phi, c, mu = (np.empty((m.nz, m.ny, m.nx)) for _ in range(3))
+        lbpf_batch_get_fields(self.ctx, i, phi, c, mu, 0)
+        return phi, c, mu
+
+    def solute_masses(self):
+        return lbpf_batch_solute_mass(self.ctx, self.n)
 
     def close(self):
         if self.ctx:

@@ -110,3 +110,24 @@ def test_params_from_workload_roundtrip(lib):
     p = L.params_from(m, "fp32")
     assert (p.nx, p.ny, p.nz, p.lattice, p.precision) == (40, 30, 1, L.LBPF_D2Q9, L.LBPF_FP32)
     assert p.lambda_ == m.lam and p.a_at == m.a_at and p.anti_trapping == 1 and p.counter_term == 0
+
+
+def test_create_batch_validates_on_the_host(lib):
+    good = L.lbpf_default_params()
+    a = np.zeros(64 * 64)
+    bad = L.lbpf_default_params()
+    bad.lattice, bad.nz = L.LBPF_D3Q19, 4
+    b3 = np.zeros(64 * 64 * 4)
+    with pytest.raises(L.LbpfError) as ei:
+        L.lbpf_create_batch([good, bad], [a, b3], [a, b3])
+    assert ei.value.status == L.LBPF_EUNSUPPORTED
+    bad = L.lbpf_default_params()
+    bad.mass_every = 1
+    with pytest.raises(L.LbpfError) as ei:
+        L.lbpf_create_batch([good, bad], [a, a], [a, a])
+    assert ei.value.status == L.LBPF_EUNSUPPORTED
+    bad = L.lbpf_default_params()
+    bad.tau_h = -1.0
+    with pytest.raises(L.LbpfError) as ei:
+        L.lbpf_create_batch([good, bad], [a, a], [a, a])
+    assert ei.value.status == L.LBPF_EINVAL and "instance 1" in str(ei.value)
