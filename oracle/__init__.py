@@ -8,4 +8,5 @@ nothing from the product.
 from .oracle import (  # noqa: F401
     OracleParams, Oracle, build, lattice_tables, gradient, lambda_star_printed,
     stefan_one_sided_root, stefan_two_sided_root,
+    PARAM_NAMES, step_adjoint, init_adjoint, trajectory_gradient, tangent_trajectory, tangent_step,
 )

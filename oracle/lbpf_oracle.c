@@ -422,3 +422,285 @@ void or_mu(const or_params *p, const double *phi, const double *c, double *mu)
     long N = (long)p->nx * p->ny * p->nz;
     for (long i = 0; i < N; ++i) mu[i] = closure_mu(p, phi[i], c[i]);
 }
+
+/* ======================================================================== */
+/* Discrete adjoint (reverse mode) of one step and of the initialisation.    */
+/*                                                                          */
+/* The step is linear in the populations and a smooth function of phi and c; */
+/* its adjoint is the chain rule taken back through the operations listed at */
+/* the top of this file, in reverse order.  Parameters differentiated:       */
+/* pb[0] = d/dD_l, pb[1] = d/dtau_g, pb[2] = d/dtau_h, pb[3] = d/dlambda,     */
+/* with W, D_s, the coexistence values and a of j_at held fixed.             */
+/* ======================================================================== */
+#ifndef ORACLE_TANGENT_BUILD
+
+/* Node that consumes the post-collision population j of node (x,y,z) when it
+ * streams: x + e_j (wrapped), or -1 when x + e_j lies beyond a bounce-back wall
+ * (the population then returns to the node itself as direction opp(j)). */
+static long downstream_index(const or_params *p, const lattice *L, int j, int x, int y, int z)
+{
+    int n[3] = {p->nx, p->ny, p->nz};
+    int c[3] = {x + L->e[j][0], y + L->e[j][1], z + L->e[j][2]};
+    for (int a = 0; a < 3; ++a) {
+        if (c[a] < 0 || c[a] >= n[a]) {
+            if (p->bc[a] == 1) return -1;
+            c[a] = wrap(c[a], n[a]);
+        }
+    }
+    return idx(p, c[0], c[1], c[2]);
+}
+
+/* Adjoint of the pointwise sources at one node.  Given the adjoints Gb[j] of the
+ * phi sources G_j, heqb[j] of the equilibria h^eq_j, Hb[j] of the c sources H_j
+ * and atb of the anti-trapping magnitude, add the adjoints of phi, mu, n, grad
+ * and of the parameters.  (Forward: Sec. 3.2 and Sec. 3.3 formulas above.) */
+static void pointwise_adjoint(const or_params *p, const lattice *L, double phi, double c, double mu,
+                              double dphi, const double grad[3], const double nvec[3],
+                              const double *Gb, const double *heqb, const double *Hb,
+                              double *phib, double *mub, double gradb[3], double nb[3], double *cb,
+                              double *dphib, double *pb)
+{
+    int q = L->q;
+    double M = p->tau_g / 3.0;
+    double W2 = p->W * p->W;
+    double dc = p->c_s_co - p->c_l_co;
+    double gamma = 3.0 / p->tau_h;
+    double D = p->D_l * phi + p->D_s * (1.0 - phi);
+    double Dprime = p->D_l - p->D_s;
+
+    /* G_j = w_j (Gst + Gcurv_j) */
+    double Gstb = 0.0;
+    for (int j = 0; j < q; ++j) Gstb += L->w[j] * Gb[j];
+    double S = 6.0 * phi * (1.0 - phi) * dc * (mu - p->mu_eq);
+    double Sb = Gstb * (-p->lambda * M / W2);
+    pb[3] += Gstb * (-M * S / W2);
+    pb[1] += Gstb * (-p->lambda * S / W2) / 3.0;
+    *phib += Sb * 6.0 * dc * (1.0 - 2.0 * phi) * (mu - p->mu_eq);
+    *mub += Sb * 6.0 * dc * phi * (1.0 - phi);
+    if (p->counter_term) {
+        double K = (4.0 / p->W) * phi * (1.0 - phi);
+        double Kb = 0.0;
+        for (int j = 0; j < q; ++j) {
+            double en = L->e[j][0] * nvec[0] + L->e[j][1] * nvec[1] + L->e[j][2] * nvec[2];
+            Kb += L->w[j] * en * Gb[j];
+            for (int a = 0; a < 3; ++a) nb[a] += K * L->w[j] * L->e[j][a] * Gb[j];
+        }
+        *phib += Kb * (4.0 / p->W) * (1.0 - 2.0 * phi);
+    } else {
+        double wp = 2.0 * phi * (1.0 - phi) * (1.0 - 2.0 * phi);
+        double wpp = 2.0 - 12.0 * phi + 12.0 * phi * phi;
+        double Gcb = 0.0;
+        for (int j = 0; j < q; ++j) Gcb += L->w[j] * Gb[j];
+        *phib += Gcb * (-(8.0 * M / W2)) * wpp;
+        pb[1] += Gcb * (-(8.0 / W2)) * wp / 3.0;
+    }
+
+    /* h^eq_0 = c - (1 - w_0) gamma D mu, h^eq_k = w_k gamma D mu */
+    double Qb = -(1.0 - L->w[0]) * heqb[0];
+    *cb += heqb[0];
+    for (int k = 1; k < q; ++k) Qb += L->w[k] * heqb[k];
+    double gammab = Qb * D * mu;
+    double Db = Qb * gamma * mu;
+    *mub += Qb * gamma * D;
+    *phib += Db * Dprime;
+    pb[0] += Db * phi;
+
+    /* H_k = gamma w_k e_k.F, F = mu D' grad + at n, at = s a W dc dphi */
+    double F[3];
+    double at = p->anti_trapping ? p->a_at * p->W * dc * dphi : 0.0;
+    for (int a = 0; a < 3; ++a) F[a] = mu * Dprime * grad[a] + at * nvec[a];
+    double Fb[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < q; ++k) {
+        double eF = L->e[k][0] * F[0] + L->e[k][1] * F[1] + L->e[k][2] * F[2];
+        gammab += L->w[k] * eF * Hb[k];
+        for (int a = 0; a < 3; ++a) Fb[a] += gamma * L->w[k] * L->e[k][a] * Hb[k];
+    }
+    double Fg = Fb[0] * grad[0] + Fb[1] * grad[1] + Fb[2] * grad[2];
+    double Fn = Fb[0] * nvec[0] + Fb[1] * nvec[1] + Fb[2] * nvec[2];
+    *mub += Dprime * Fg;
+    pb[0] += mu * Fg;
+    for (int a = 0; a < 3; ++a) {
+        gradb[a] += mu * Dprime * Fb[a];
+        nb[a] += at * Fb[a];
+    }
+    if (p->anti_trapping) *dphib += p->a_at * p->W * dc * Fn;
+    pb[2] += gammab * (-3.0 / (p->tau_h * p->tau_h));
+}
+
+/* Adjoint of the unit normal and of the closure, then the transpose of the
+ * gradient stencil: the last three operations of every node, reversed. */
+static void finish_adjoint(const or_params *p, const lattice *L, const double *grad, const double *nvec,
+                           double *gradb, double *nb, double *mub, double *phib, double *cb)
+{
+    long N = (long)p->nx * p->ny * p->nz;
+    for (long i = 0; i < N; ++i) {
+        const double *gr = grad + 3 * i, *nv = nvec + 3 * i;
+        double g2 = gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2];
+        double inv = 1.0 / sqrt(g2 + p->eps_n * p->eps_n);
+        double nn = nv[0] * nb[3 * i] + nv[1] * nb[3 * i + 1] + nv[2] * nb[3 * i + 2];
+        for (int a = 0; a < 3; ++a) gradb[3 * i + a] += (nb[3 * i + a] - nv[a] * nn) * inv;
+        cb[i] += mub[i];
+        phib[i] += mub[i] * (p->c_s_co - p->c_l_co);
+    }
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) {
+                long i = idx(p, x, y, z);
+                for (int k = 1; k < L->q; ++k) {
+                    const int *e = L->e[k];
+                    double t = 1.5 * L->w[k] * (e[0] * gradb[3 * i] + e[1] * gradb[3 * i + 1] + e[2] * gradb[3 * i + 2]);
+                    phib[stencil_index(p, x + e[0], y + e[1], z + e[2])] += t;
+                    phib[stencil_index(p, x - e[0], y - e[1], z - e[2])] -= t;
+                }
+            }
+}
+
+/* Adjoint of one step.  (g, h, phi, c): the state at step n.  On entry gb, hb,
+ * phib, cb hold the adjoints of the state at step n+1; on return they hold the
+ * adjoints of the state at step n.  pb[4] accumulates the parameter adjoints.
+ * Returns 0, or -1 on allocation failure. */
+int or_step_adjoint(const or_params *p, const double *g, const double *h, const double *phi, const double *c,
+                    double *gb, double *hb, double *phib, double *cb, double *pb)
+{
+    lattice L = get_lattice(p->dim);
+    long N = (long)p->nx * p->ny * p->nz;
+    int q = L.q;
+    double omg = 1.0 / (p->tau_g + 0.5), omh = 1.0 / (p->tau_h + 0.5);
+    double *mu = malloc(sizeof(double) * N), *grad = malloc(sizeof(double) * 3 * N);
+    double *nvec = malloc(sizeof(double) * 3 * N), *gs = malloc(sizeof(double) * q * N);
+    double *phinew = malloc(sizeof(double) * N), *Gsum = malloc(sizeof(double) * N);
+    double *gbo = malloc(sizeof(double) * q * N), *hbo = malloc(sizeof(double) * q * N);
+    double *phibo = calloc(N, sizeof(double)), *cbo = calloc(N, sizeof(double));
+    double *mub = calloc(N, sizeof(double)), *gradb = calloc(3 * N, sizeof(double));
+    double *nb = calloc(3 * N, sizeof(double)), *dphib = calloc(N, sizeof(double));
+    int rc = 0;
+    if (!mu || !grad || !nvec || !gs || !phinew || !Gsum || !gbo || !hbo || !phibo || !cbo || !mub || !gradb ||
+        !nb || !dphib) rc = -1;
+    if (rc == 0) {
+        /* forward recomputation of the step's intermediates */
+        for (int z = 0; z < p->nz; ++z)
+            for (int y = 0; y < p->ny; ++y)
+                for (int x = 0; x < p->nx; ++x) {
+                    long i = idx(p, x, y, z);
+                    mu[i] = closure_mu(p, phi[i], c[i]);
+                    gradient_at(p, &L, phi, x, y, z, grad + 3 * i);
+                    normal_from(p, grad + 3 * i, nvec + 3 * i);
+                    double s = 0.0;
+                    for (int k = 0; k < q; ++k) {
+                        double Gk = source_G(p, &L, k, phi[i], mu[i], nvec + 3 * i);
+                        double geq_tilde = L.w[k] * phi[i] - 0.5 * Gk;
+                        gs[k * N + i] = g[k * N + i] - omg * (g[k * N + i] - geq_tilde) + Gk;
+                        s += Gk;
+                    }
+                    Gsum[i] = s;
+                }
+        for (int z = 0; z < p->nz; ++z)
+            for (int y = 0; y < p->ny; ++y)
+                for (int x = 0; x < p->nx; ++x) {
+                    long i = idx(p, x, y, z);
+                    double s = 0.0;
+                    for (int k = 0; k < q; ++k) {
+                        long src = upstream_index(p, &L, k, x, y, z);
+                        s += (src < 0) ? gs[L.opp[k] * N + i] : gs[k * N + src];
+                    }
+                    phinew[i] = s + 0.5 * Gsum[i];
+                }
+        /* composition part, reversed: c' = sum h', stream, collision, sources */
+        for (int z = 0; z < p->nz; ++z)
+            for (int y = 0; y < p->ny; ++y)
+                for (int x = 0; x < p->nx; ++x) {
+                    long i = idx(p, x, y, z);
+                    double dphi = phinew[i] - phi[i];
+                    double hsb[19], heqb[19], Hb[19], Gb0[19];
+                    double F[3];
+                    flux_F(p, mu[i], dphi, grad + 3 * i, nvec + 3 * i, F);
+                    double omhb = 0.0;
+                    for (int j = 0; j < q; ++j) {
+                        long y2 = downstream_index(p, &L, j, x, y, z);
+                        hsb[j] = (y2 < 0) ? hb[L.opp[j] * N + i] + cb[i] : hb[j * N + y2] + cb[y2];
+                        double Hj = source_H(p, &L, j, F);
+                        double heq = h_equilibrium(p, &L, j, phi[i], c[i], mu[i]);
+                        hbo[j * N + i] = (1.0 - omh) * hsb[j];
+                        heqb[j] = omh * hsb[j];
+                        Hb[j] = (1.0 - 0.5 * omh) * hsb[j];
+                        omhb += hsb[j] * (heq - 0.5 * Hj - h[j * N + i]);
+                        Gb0[j] = 0.0;
+                    }
+                    pb[2] += omhb * (-omh * omh);
+                    pointwise_adjoint(p, &L, phi[i], c[i], mu[i], dphi, grad + 3 * i, nvec + 3 * i, Gb0, heqb, Hb,
+                                      phibo + i, mub + i, gradb + 3 * i, nb + 3 * i, cbo + i, dphib + i, pb);
+                }
+        /* phi part, reversed: phi' = sum g' + G/2, stream, collision, sources */
+        for (int z = 0; z < p->nz; ++z)
+            for (int y = 0; y < p->ny; ++y)
+                for (int x = 0; x < p->nx; ++x) {
+                    long i = idx(p, x, y, z);
+                    double Gb[19], zero[19], dummy = 0.0;
+                    double omgb = 0.0, phinewb_here = phib[i] + dphib[i];
+                    for (int j = 0; j < q; ++j) {
+                        long y2 = downstream_index(p, &L, j, x, y, z);
+                        double gsb = (y2 < 0) ? gb[L.opp[j] * N + i] + phinewb_here
+                                              : gb[j * N + y2] + phib[y2] + dphib[y2];
+                        double Gj = source_G(p, &L, j, phi[i], mu[i], nvec + 3 * i);
+                        gbo[j * N + i] = (1.0 - omg) * gsb;
+                        phibo[i] += omg * L.w[j] * gsb;
+                        Gb[j] = (1.0 - 0.5 * omg) * gsb + 0.5 * phinewb_here;
+                        omgb += gsb * (L.w[j] * phi[i] - 0.5 * Gj - g[j * N + i]);
+                        zero[j] = 0.0;
+                    }
+                    pb[1] += omgb * (-omg * omg);
+                    phibo[i] -= dphib[i];                 /* dphi = phi' - phi */
+                    pointwise_adjoint(p, &L, phi[i], c[i], mu[i], 0.0, grad + 3 * i, nvec + 3 * i, Gb, zero, zero,
+                                      phibo + i, mub + i, gradb + 3 * i, nb + 3 * i, cbo + i, &dummy, pb);
+                }
+        finish_adjoint(p, &L, grad, nvec, gradb, nb, mub, phibo, cbo);
+        memcpy(gb, gbo, sizeof(double) * q * N);
+        memcpy(hb, hbo, sizeof(double) * q * N);
+        memcpy(phib, phibo, sizeof(double) * N);
+        memcpy(cb, cbo, sizeof(double) * N);
+    }
+    free(mu); free(grad); free(nvec); free(gs); free(phinew); free(Gsum); free(gbo); free(hbo);
+    free(phibo); free(cbo); free(mub); free(gradb); free(nb); free(dphib);
+    return rc;
+}
+
+/* Adjoint of or_init.  On entry gb, hb hold the adjoints of the initial
+ * populations and phib, cb those of the initial fields; on return phib, cb
+ * hold the adjoints of phi0 and c0.  pb[4] accumulates the parameter adjoints. */
+int or_init_adjoint(const or_params *p, const double *phi0, const double *c0, const double *gb, const double *hb,
+                    double *phib, double *cb, double *pb)
+{
+    lattice L = get_lattice(p->dim);
+    long N = (long)p->nx * p->ny * p->nz;
+    int q = L.q;
+    double *mu = malloc(sizeof(double) * N), *grad = malloc(sizeof(double) * 3 * N);
+    double *nvec = malloc(sizeof(double) * 3 * N), *mub = calloc(N, sizeof(double));
+    double *gradb = calloc(3 * N, sizeof(double)), *nb = calloc(3 * N, sizeof(double));
+    int rc = (mu && grad && nvec && mub && gradb && nb) ? 0 : -1;
+    if (rc == 0) {
+        for (int z = 0; z < p->nz; ++z)
+            for (int y = 0; y < p->ny; ++y)
+                for (int x = 0; x < p->nx; ++x) {
+                    long i = idx(p, x, y, z);
+                    mu[i] = closure_mu(p, phi0[i], c0[i]);
+                    gradient_at(p, &L, phi0, x, y, z, grad + 3 * i);
+                    normal_from(p, grad + 3 * i, nvec + 3 * i);
+                }
+        for (long i = 0; i < N; ++i) {
+            /* g_k = w_k phi0 - G_k/2,  h_k = h^eq_k - H_k/2 with dphi/dt = 0 */
+            double Gb[19], heqb[19], Hb[19], dummy = 0.0;
+            for (int j = 0; j < q; ++j) {
+                phib[i] += L.w[j] * gb[j * N + i];
+                Gb[j] = -0.5 * gb[j * N + i];
+                heqb[j] = hb[j * N + i];
+                Hb[j] = -0.5 * hb[j * N + i];
+            }
+            pointwise_adjoint(p, &L, phi0[i], c0[i], mu[i], 0.0, grad + 3 * i, nvec + 3 * i, Gb, heqb, Hb,
+                              phib + i, mub + i, gradb + 3 * i, nb + 3 * i, cb + i, &dummy, pb);
+        }
+        finish_adjoint(p, &L, grad, nvec, gradb, nb, mub, phib, cb);
+    }
+    free(mu); free(grad); free(nvec); free(mub); free(gradb); free(nb);
+    return rc;
+}
+#endif /* ORACLE_TANGENT_BUILD */

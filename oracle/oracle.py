@@ -22,19 +22,28 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbpf_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "liblbpf_oracle.so")
+_SRC_CS = os.path.join(_HERE, "tangent_cs.c")
+_LIB_CS = os.path.join(_HERE, "_build", "liblbpf_oracle_cs.so")
 _lib = None
+_lib_cs = None
+
+
+def _compile(src, lib, deps, force):
+    os.makedirs(os.path.dirname(lib), exist_ok=True)
+    stale = (not os.path.exists(lib)) or any(os.path.getmtime(lib) < os.path.getmtime(d) for d in deps)
+    if force or stale:
+        tmp = lib + ".%d.tmp" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-std=c99",
+                               "-shared", "-fPIC", "-o", tmp, src, "-lm"])
+        os.replace(tmp, lib)
+    return lib
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (no FMA contraction, OpenMP over rows)."""
-    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    stale = (not os.path.exists(_LIB)) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC)
-    if force or stale:
-        tmp = _LIB + ".%d.tmp" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-std=c99",
-                               "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+    """Compile the oracle and its complex-step build with gcc (no FMA
+    contraction, OpenMP over rows)."""
+    _compile(_SRC_CS, _LIB_CS, [_SRC, _SRC_CS], force)
+    return _compile(_SRC, _LIB, [_SRC], force)
 
 
 def _load():
@@ -50,7 +59,20 @@ def _load():
                                     ctypes.POINTER(ctypes.c_int)]
         _lib.or_set_threads.argtypes = [ctypes.c_int]
         _lib.or_get_threads.restype = ctypes.c_int
+        _lib.or_step_adjoint.argtypes = [ctypes.c_void_p] + [dp] * 9
+        _lib.or_init_adjoint.argtypes = [ctypes.c_void_p] + [dp] * 7
     return _lib
+
+
+def _load_cs():
+    global _lib_cs
+    if _lib_cs is None:
+        build()
+        _lib_cs = ctypes.CDLL(_LIB_CS)
+        vp = ctypes.c_void_p
+        _lib_cs.or_init.argtypes = [vp] * 7
+        _lib_cs.or_step.argtypes = [vp] * 5 + [ctypes.c_int]
+    return _lib_cs
 
 
 class _CParams(ctypes.Structure):
@@ -107,6 +129,19 @@ class OracleParams:
         c.counter_term, c.anti_trapping = int(self.counter_term), int(self.anti_trapping)
         c.a_at, c.eps_n = self.a_at, self.eps_n
         return c
+
+
+class _CParamsCS(ctypes.Structure):
+    """or_params of the complex-step build: every double is a (re, im) pair."""
+    _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("nz", ctypes.c_int), ("bc", ctypes.c_int * 3), ("pad", ctypes.c_int),
+                ("tau_g", ctypes.c_double * 2), ("tau_h", ctypes.c_double * 2),
+                ("W", ctypes.c_double * 2), ("lam", ctypes.c_double * 2),
+                ("D_l", ctypes.c_double * 2), ("D_s", ctypes.c_double * 2),
+                ("c_s_co", ctypes.c_double * 2), ("c_l_co", ctypes.c_double * 2),
+                ("mu_eq", ctypes.c_double * 2), ("counter_term", ctypes.c_int),
+                ("anti_trapping", ctypes.c_int), ("a_at", ctypes.c_double * 2),
+                ("eps_n", ctypes.c_double * 2)]
 
 
 def _dp(a: np.ndarray):
@@ -235,3 +270,107 @@ def stefan_two_sided_root(D_s, D_l, m_s, m_l, df_min, cs_inf, cl_inf) -> float:
                 + 0.5 * a * dm * dm)
 
     return _brent(f, -2.0, 2.0)
+
+
+# ---- discrete adjoint and complex-step tangents -------------------------------
+
+PARAM_NAMES = ("D_l", "tau_g", "tau_h", "lam")
+
+
+def step_adjoint(p: OracleParams, g, h, phi, c, gb, hb, phib, cb):
+    """Adjoint of one step at state (g, h, phi, c): maps the adjoints of the state
+    at n+1 to those at n; returns (gb, hb, phib, cb, pb) with pb the adjoints of
+    (D_l, tau_g, tau_h, lambda)."""
+    cp = p._c()
+    arrs = [np.ascontiguousarray(a, dtype=np.float64).copy() for a in (gb, hb, phib, cb)]
+    st = [np.ascontiguousarray(a, dtype=np.float64) for a in (g, h, phi, c)]
+    pb = np.zeros(4)
+    rc = _load().or_step_adjoint(ctypes.byref(cp), *[_dp(a) for a in st], *[_dp(a) for a in arrs], _dp(pb))
+    if rc != 0:
+        raise MemoryError("oracle adjoint failed")
+    return (*arrs, pb)
+
+
+def init_adjoint(p: OracleParams, phi0, c0, gb, hb, phib, cb):
+    """Adjoint of the initialisation: returns (adjoint of phi0, of c0, pb)."""
+    cp = p._c()
+    phi0 = np.ascontiguousarray(phi0, dtype=np.float64)
+    c0 = np.ascontiguousarray(c0, dtype=np.float64)
+    gb = np.ascontiguousarray(gb, dtype=np.float64)
+    hb = np.ascontiguousarray(hb, dtype=np.float64)
+    phib = np.ascontiguousarray(phib, dtype=np.float64).copy()
+    cb = np.ascontiguousarray(cb, dtype=np.float64).copy()
+    pb = np.zeros(4)
+    rc = _load().or_init_adjoint(ctypes.byref(cp), _dp(phi0), _dp(c0), _dp(gb), _dp(hb), _dp(phib), _dp(cb),
+                                 _dp(pb))
+    if rc != 0:
+        raise MemoryError("oracle adjoint failed")
+    return phib, cb, pb
+
+
+def trajectory_gradient(p: OracleParams, phi0, c0, nsteps, phib_final, cb_final):
+    """Gradient of L(phi_n, c_n) given dL/dphi_n, dL/dc_n after nsteps steps from
+    (phi0, c0): forward storing every state, then the adjoint steps in reverse and
+    the adjoint of the initialisation.  Returns (dL/dphi0, dL/dc0, dL/dparams)."""
+    o = Oracle(p, phi0, c0)
+    states = [(o.g.copy(), o.h.copy(), o.phi.copy(), o.c.copy())]
+    for _ in range(nsteps):
+        o.step(1)
+        states.append((o.g.copy(), o.h.copy(), o.phi.copy(), o.c.copy()))
+    gb = np.zeros_like(o.g)
+    hb = np.zeros_like(o.h)
+    phib = np.ascontiguousarray(phib_final, dtype=np.float64).reshape(p.shape).copy()
+    cb = np.ascontiguousarray(cb_final, dtype=np.float64).reshape(p.shape).copy()
+    ptot = np.zeros(4)
+    for n in range(nsteps - 1, -1, -1):
+        gb, hb, phib, cb, pb = step_adjoint(p, *states[n], gb, hb, phib, cb)
+        ptot += pb
+    phi0b, c0b, pb = init_adjoint(p, phi0, c0, gb, hb, phib, cb)
+    return phi0b, c0b, ptot + pb
+
+
+def _cs_params(p: OracleParams, dparams, h):
+    c = _CParamsCS()
+    c.dim, c.nx, c.ny, c.nz = p.dim, p.nx, p.ny, p.nz
+    for a in range(3):
+        c.bc[a] = int(p.bc[a])
+    d = dict(zip(PARAM_NAMES, dparams if dparams is not None else (0.0,) * 4))
+    for name in ("tau_g", "tau_h", "W", "lam", "D_l", "D_s", "c_s_co", "c_l_co", "mu_eq", "a_at", "eps_n"):
+        getattr(c, name)[0] = getattr(p, name)
+        getattr(c, name)[1] = h * d.get(name, 0.0)
+    c.counter_term, c.anti_trapping = int(p.counter_term), int(p.anti_trapping)
+    return c
+
+
+def tangent_trajectory(p: OracleParams, phi0, c0, nsteps, dphi0=None, dc0=None, dparams=None, h=1e-30):
+    """Exact directional derivative (complex step) of the state after nsteps steps
+    along (dphi0, dc0, dparams); returns (dg, dh, dphi, dc)."""
+    lib = _load_cs()
+    cp = _cs_params(p, dparams, h)
+    shp = p.shape
+    q = 19 if p.dim == 3 else 9
+    z = lambda a: np.zeros(shp) if a is None else np.asarray(a, dtype=np.float64).reshape(shp)
+    phi0c = np.ascontiguousarray(np.asarray(phi0, dtype=np.float64).reshape(shp) + 1j * h * z(dphi0))
+    c0c = np.ascontiguousarray(np.asarray(c0, dtype=np.float64).reshape(shp) + 1j * h * z(dc0))
+    g = np.zeros((q,) + shp, complex)
+    hh = np.zeros((q,) + shp, complex)
+    phi = np.zeros(shp, complex)
+    c = np.zeros(shp, complex)
+    P = lambda a: a.ctypes.data
+    lib.or_init(ctypes.byref(cp), P(phi0c), P(c0c), P(g), P(hh), P(phi), P(c))
+    if nsteps:
+        lib.or_step(ctypes.byref(cp), P(g), P(hh), P(phi), P(c), int(nsteps))
+    return g.imag / h, hh.imag / h, phi.imag / h, c.imag / h
+
+
+def tangent_step(p: OracleParams, g, hpop, phi, c, dg, dh, dphi, dc, dparams=None, h=1e-30):
+    """Exact directional derivative (complex step) of one step from state
+    (g, h, phi, c) along (dg, dh, dphi, dc, dparams)."""
+    lib = _load_cs()
+    cp = _cs_params(p, dparams, h)
+    G = np.ascontiguousarray(g + 1j * h * dg)
+    H = np.ascontiguousarray(hpop + 1j * h * dh)
+    F = np.ascontiguousarray(phi + 1j * h * dphi)
+    C = np.ascontiguousarray(c + 1j * h * dc)
+    lib.or_step(ctypes.byref(cp), G.ctypes.data, H.ctypes.data, F.ctypes.data, C.ctypes.data, 1)
+    return G.imag / h, H.imag / h, F.imag / h, C.imag / h
