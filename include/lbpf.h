@@ -98,7 +98,8 @@ typedef struct {
     double eps_n;                /* regularisation of |grad phi| in n; default 1e-12 */
     int32_t mass_every;          /* steps between FP64 mass corrections, 0 = off (see
                                     lbpf_solute_mass); FP32 and 16-bit modes want 1 */
-    int32_t reserved;            /* set to 0 */
+    int32_t checkpoint_every;    /* 0: no adjoint; k > 0: record the state every k
+                                    steps for lbpf_adjoint_step (FP64 and FP32 only) */
 } lbpf_params;
 
 typedef struct lbpf_ctx lbpf_ctx;
@@ -227,6 +228,44 @@ lbpf_status lbpf_batch_solute_mass(lbpf_ctx *ctx, double *masses);
  * n > LBPF_NOALLOC_MAX_ELEMENTS or another precision; ECUDA. */
 lbpf_status lbpf_mass_noalloc(const void *c, const void *phi, int64_t n, int32_t precision,
                               double *out_device, void *cuda_stream);
+
+/* Number of parameter adjoints that lbpf_adjoint_step returns, in this order:
+ * dL/dD_l, dL/dtau_g, dL/dtau_h, dL/dlambda, dL/da, dL/dD_s. */
+#define LBPF_ADJ_NPARAMS 6
+
+/* Discrete adjoint (reverse mode) of the whole trajectory since creation: the
+ * gradient of a scalar loss L(phi_T, c_T) of the current fields with respect to
+ * the initial fields and the parameters, exact for the discrete scheme (the
+ * time step of Sec. 3 and the initialisation of lbpf_create, differentiated
+ * by hand).  The paper does not differentiate its scheme; this makes the step a
+ * differentiable layer.
+ *   dL_dphi, dL_dc    FP64 [nz][ny][nx]: dL/dphi_T and dL/dc_T (NULL = zero).
+ *   dL_dphi0, dL_dc0  FP64 [nz][ny][nx] outputs: dL/dphi0 and dL/dc0 (either
+ *                     may be NULL).
+ *   ptr_is_device     where those four arrays live (as for lbpf_get_fields).
+ *   dL_dparams        host array of LBPF_ADJ_NPARAMS doubles, overwritten:
+ *                     dL/dD_l, dL/dtau_g, dL/dtau_h, dL/dlambda, dL/da, dL/dD_s
+ *                     in the units of lbpf_params (D_l, D_s physical when
+ *                     dx, dt != 1).  When a_at < 0 selects a = (1 - D_s/D_l)/4,
+ *                     the D_l and D_s entries include that dependence; dL/da is
+ *                     the partial derivative at fixed D_l, D_s (0 without
+ *                     anti-trapping).  The kinetic coefficient M_phi = tau_g/3
+ *                     in lattice units, so dL/dM_phi = 3 dL/dtau_g.
+ * Needs checkpoint_every = k > 0 at creation: the context then copies the
+ * state (populations, fields, mass-correction state) every k steps.  The
+ * sweep runs the segments in reverse: it restores a checkpoint, re-runs the
+ * segment's forward steps into per-step storage (k + 1 states, allocated on the
+ * first call and kept), then runs the adjoint steps back over it, three kernels
+ * per step.  The mass correction (mass_every > 0) is replayed bit for bit and
+ * treated as a constant shift (its derivative is not taken).  Parameter
+ * adjoints are summed in FP64 in a fixed order (deterministic); the field
+ * adjoints are computed in the context's precision.  The forward state is left
+ * unchanged.  Synchronises the stream.
+ * Errors: EINVAL (NULL ctx or dL_dparams), EUNSUPPORTED (checkpoint_every was
+ * 0, a batch, or a 16-bit storage mode), ENOMEM, ECUDA, ESTATE. */
+lbpf_status lbpf_adjoint_step(lbpf_ctx *ctx, const double *dL_dphi, const double *dL_dc,
+                              double *dL_dphi0, double *dL_dc0, int32_t ptr_is_device,
+                              double *dL_dparams);
 
 /* Number of coupled steps taken since creation. */
 lbpf_status lbpf_get_step(const lbpf_ctx *ctx, int64_t *step);

@@ -10,7 +10,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libgb_lbpf.so")
-SOURCES = ["lbpf.cu", "noalloc.cu"]
+SOURCES = ["lbpf.cu", "adjoint.cu", "noalloc.cu"]
+OBJDIR = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -21,19 +22,32 @@ def _deps():
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every CUDA source into one shared library next to this file."""
+    """Compile every CUDA source (in parallel, one object each) and link them
+    into one shared library next to this file."""
     stale = force or not os.path.exists(LIB) or any(
         os.path.getmtime(f) > os.path.getmtime(LIB) for f in _deps())
     if not stale:
         return LIB
     nvcc = os.environ.get("NVCC", "nvcc")
-    tmp = LIB + ".%d.tmp" % os.getpid()
     extra = os.environ.get("LBPF_NVCC_FLAGS", "").split()
-    cmd = [nvcc, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
-           "-I" + INCLUDE, "-I" + CSRC, *extra, "-o", tmp] + [os.path.join(CSRC, s) for s in SOURCES]
-    if verbose:
-        print(" ".join(cmd), file=sys.stderr)
-    subprocess.check_call(cmd)
+    os.makedirs(OBJDIR, exist_ok=True)
+    common = [nvcc, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE,
+              "-I" + CSRC, *extra]
+    procs, objs = [], []
+    for src in SOURCES:
+        obj = os.path.join(OBJDIR, src.replace(".cu", ".%d.o" % os.getpid()))
+        cmd = common + ["-c", os.path.join(CSRC, src), "-o", obj]
+        if verbose:
+            print(" ".join(cmd), file=sys.stderr)
+        procs.append(subprocess.Popen(cmd))
+        objs.append(obj)
+    failed = [SOURCES[i] for i, pr in enumerate(procs) if pr.wait() != 0]
+    if failed:
+        raise RuntimeError("nvcc failed on " + ", ".join(failed))
+    tmp = LIB + ".%d.tmp" % os.getpid()
+    subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *objs])
+    for o in objs:
+        os.remove(o)
     os.replace(tmp, LIB)
     return LIB
 

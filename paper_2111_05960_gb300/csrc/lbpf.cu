@@ -13,92 +13,56 @@
 #include <string>
 #include <vector>
 
-#include "lbpf.h"
-#include "step_kernels.cuh"
-#include "batch_kernels.cuh"
+#include "context.cuh"
 
 using namespace lbpf;
+using namespace lbpf_rt;
 
 namespace {
-
 thread_local std::string g_thread_error;
-
-struct Dispatch;
-struct BatchDispatch;
-
 }  // namespace
 
 void lbpf_internal_set_thread_error(const std::string& msg) { g_thread_error = msg; }
 
-struct lbpf_ctx {
-    lbpf_params p;
-    StepParams sp;
-    KParams kp;
-    int q = 0;
-    size_t real_size = 0, store_size = 0;
-    cudaStream_t stream = nullptr;
-    int device = 0;
-    void* g[2] = {nullptr, nullptr};
-    void* h[2] = {nullptr, nullptr};
-    void* phi[2] = {nullptr, nullptr};
-    void* c[2] = {nullptr, nullptr};
-    double* staging = nullptr;     // 3 N doubles, allocated on first host transfer
-    double* partials = nullptr;    // mass reduction scratch
-    double* mass_out = nullptr;    // 3 doubles
-    double* corr_partials = nullptr;   // one FP64 mass per composition-kernel block
-    MassCorr* corr = nullptr;          // closed-loop mass correction state (device)
-    int corr_blocks = 0;
-    long long corr_stride = 1;
-    int mass_blocks = 0;
-    int cur = 0;
-    int64_t step = 0;
-    bool poisoned = false;
-    std::string err;
-    const Dispatch* ops = nullptr;
-    // a batch of 2-D instances (lbpf_create_batch)
-    bool is_batch = false;
-    int nb = 0;
-    std::vector<BatchInst> binst;      // host copy of the instance table
-    BatchInst* d_binst = nullptr;
-    int* d_tile_inst = nullptr;
-    int ntiles = 0;
-    int persist_blocks = 0;
-    const BatchDispatch* bops = nullptr;
-    // two steps captured as a CUDA graph (replayed by lbpf_step)
-    cudaGraphExec_t graph = nullptr;
-    bool graph_failed = false;
-};
+// ---- helpers shared with adjoint.cu ---------------------------------------------
 
-namespace {
-
-lbpf_status fail(lbpf_ctx* ctx, lbpf_status st, const std::string& msg) {
+lbpf_status lbpf_rt::fail(lbpf_ctx* ctx, lbpf_status st, const std::string& msg) {
     if (ctx) ctx->err = msg; else g_thread_error = msg;
     return st;
 }
 
-lbpf_status cuda_fail(lbpf_ctx* ctx, cudaError_t e, const char* what) {
+lbpf_status lbpf_rt::cuda_fail(lbpf_ctx* ctx, cudaError_t e, const char* what) {
     std::string m = std::string(what) + ": " + cudaGetErrorString(e);
     return fail(ctx, e == cudaErrorMemoryAllocation ? LBPF_ENOMEM : LBPF_ECUDA, m);
 }
 
-#define LBPF_CUDA(ctx, call)                                    \
-    do {                                                        \
-        cudaError_t e_ = (call);                                \
-        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
-    } while (0)
+lbpf_status lbpf_rt::alloc(lbpf_ctx* ctx, void** ptr, size_t bytes, const char* what) {
+    if (const char* f = getenv("LBPF_FAULT")) {
+        if (strcmp(f, "alloc") == 0) return fail(ctx, LBPF_ENOMEM, std::string("injected allocation failure: ") + what);
+    }
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        cudaGetLastError();
+        return cuda_fail(ctx, e, what);
+    }
+    return LBPF_OK;
+}
+
+lbpf_status lbpf_rt::ensure_staging(lbpf_ctx* ctx) {
+    if (ctx->staging) return LBPF_OK;
+    return alloc(ctx, (void**)&ctx->staging, sizeof(double) * 3 * (size_t)ctx->sp.N, "staging");
+}
+
+lbpf_status lbpf_rt::check_launch(lbpf_ctx* ctx, const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, what);
+    return LBPF_OK;
+}
+
+namespace {
 
 // ---- per (lattice, storage) dispatch ---------------------------------------------
-
-struct Dispatch {
-    lbpf_status (*prepare)(lbpf_ctx*);
-    void (*launch_phi)(lbpf_ctx*, int cur);
-    void (*launch_c)(lbpf_ctx*, int cur, double* mass_partials);
-    void (*launch_init)(lbpf_ctx*);
-    void (*launch_pops_out)(lbpf_ctx*, double* g, double* h);
-    void (*launch_corr)(lbpf_ctx*, int cur_after);
-    void (*launch_pop_mass)(lbpf_ctx*);
-    int (*c_blocks)(const lbpf_ctx*);
-};
 
 // Tile shapes: 32 x BY threads per block, ZCH planes per block in 3-D, at least
 // MINB resident blocks per SM (register budget).  Overridable at build time.
@@ -163,19 +127,27 @@ struct Impl {
         const int zblocks = L::D == 3 ? (P.nz + ZCH - 1) / ZCH : 1;
         return dim3((P.nx + 31) / 32, (P.ny + BY - 1) / BY, zblocks);
     }
+    static void launch_phi_p(lbpf_ctx* ctx, const void* g, void* g_out, const void* phi, const void* c,
+                             void* phi_out) {
+        auto kern = walls(ctx) ? k_phi_step<L, SP, BY, ZCH, MINB, true> : k_phi_step<L, SP, BY, ZCH, MINB, false>;
+        kern<<<grid(ctx), dim3(32, BY), smem_phi, ctx->stream>>>(ctx->kp, (const S*)g, (S*)g_out, (const R*)phi,
+                                                                   (const R*)c, (R*)phi_out);
+    }
+    static void launch_c_p(lbpf_ctx* ctx, const void* h, void* h_out, const void* phi, const void* phi_out,
+                           const void* c, void* c_out, double* mass_partials) {
+        auto kern = walls(ctx) ? k_c_step<L, SP, BY, ZCH, MINB, true> : k_c_step<L, SP, BY, ZCH, MINB, false>;
+        kern<<<grid(ctx), dim3(32, BY), smem_c, ctx->stream>>>(ctx->kp, (const S*)h, (S*)h_out, (const R*)phi,
+                                                                 (const R*)phi_out, (const R*)c, (R*)c_out,
+                                                                 mass_partials);
+    }
     static void launch_phi(lbpf_ctx* ctx, int cur) {
         const int nxt = cur ^ 1;
-        auto kern = walls(ctx) ? k_phi_step<L, SP, BY, ZCH, MINB, true> : k_phi_step<L, SP, BY, ZCH, MINB, false>;
-        kern<<<grid(ctx), dim3(32, BY), smem_phi, ctx->stream>>>(
-            ctx->kp, (const S*)ctx->g[cur], (S*)ctx->g[nxt], (const R*)ctx->phi[cur], (const R*)ctx->c[cur],
-            (R*)ctx->phi[nxt]);
+        launch_phi_p(ctx, ctx->g[cur], ctx->g[nxt], ctx->phi[cur], ctx->c[cur], ctx->phi[nxt]);
     }
     static void launch_c(lbpf_ctx* ctx, int cur, double* mass_partials) {
         const int nxt = cur ^ 1;
-        auto kern = walls(ctx) ? k_c_step<L, SP, BY, ZCH, MINB, true> : k_c_step<L, SP, BY, ZCH, MINB, false>;
-        kern<<<grid(ctx), dim3(32, BY), smem_c, ctx->stream>>>(
-            ctx->kp, (const S*)ctx->h[cur], (S*)ctx->h[nxt], (const R*)ctx->phi[cur], (const R*)ctx->phi[nxt],
-            (const R*)ctx->c[cur], (R*)ctx->c[nxt], mass_partials);
+        launch_c_p(ctx, ctx->h[cur], ctx->h[nxt], ctx->phi[cur], ctx->phi[nxt], ctx->c[cur], ctx->c[nxt],
+                   mass_partials);
     }
     static void launch_init(lbpf_ctx* ctx) {
         const long long N = ctx->sp.N;
@@ -191,11 +163,13 @@ struct Impl {
             (const S*)ctx->h[cur], g, h);
     }
     // mass correction after a composition step whose new state has parity `cur_after`
-    static void launch_corr(lbpf_ctx* ctx, int cur_after) {
-        k_mass_corr_plan<<<1, kMassThreads, 0, ctx->stream>>>(ctx->corr_partials, ctx->corr_blocks, ctx->corr,
+    static void launch_corr_p(lbpf_ctx* ctx, MassCorr* mc, void* c, void* h) {
+        k_mass_corr_plan<<<1, kMassThreads, 0, ctx->stream>>>(ctx->corr_partials, ctx->corr_blocks, mc,
                                                              ctx->sp.N, kCorrDelta);
-        k_mass_corr_apply<SP><<<64, 256, 0, ctx->stream>>>(ctx->corr, (R*)ctx->c[cur_after],
-                                                           (S*)ctx->h[cur_after], ctx->sp.N, ctx->corr_stride);
+        k_mass_corr_apply<SP><<<64, 256, 0, ctx->stream>>>(mc, (R*)c, (S*)h, ctx->sp.N, ctx->corr_stride);
+    }
+    static void launch_corr(lbpf_ctx* ctx, int cur_after) {
+        launch_corr_p(ctx, ctx->corr, ctx->c[cur_after], ctx->h[cur_after]);
     }
     static void launch_pop_mass(lbpf_ctx* ctx) {
         k_pop_mass<L, SP><<<ctx->mass_blocks, kMassThreads, 0, ctx->stream>>>(
@@ -208,8 +182,9 @@ struct Impl {
         return (int)(g.x * g.y * g.z);
     }
     static const Dispatch* table() {
-        static const Dispatch d = {prepare, launch_phi, launch_c, launch_init, launch_pops_out,
-                                   launch_corr, launch_pop_mass, c_blocks};
+        static const Dispatch d = {prepare,         launch_phi,   launch_c,   launch_init,
+                                   launch_pops_out, launch_corr,  launch_pop_mass, c_blocks,
+                                   launch_phi_p,    launch_c_p,   launch_corr_p};
         return &d;
     }
 };
@@ -235,14 +210,6 @@ const Dispatch* pick(int lattice, int precision) {
 
 // ---- batch of 2-D instances -------------------------------------------------------
 
-struct BatchDispatch {
-    lbpf_status (*prepare)(lbpf_ctx*);
-    void (*launch_phi)(lbpf_ctx*, int cur);
-    void (*launch_c)(lbpf_ctx*, int cur);
-    void (*launch_init)(lbpf_ctx*, int i);
-    void (*fields_out)(lbpf_ctx*, int i, double* phi, double* c, double* mu);
-    void (*pop_mass)(lbpf_ctx*, int i);   // exact mass of instance i into mass_out[0]
-};
 
 template <class SP>
 struct BatchImpl {
@@ -339,6 +306,7 @@ lbpf_status validate(const lbpf_params* p, std::string& why) {
         return bad("non-finite parameter");
     if (p->anti_trapping && p->a_at < 0 && !(p->D_l > 0)) return bad("automatic a needs D_l > 0");
     if (p->mass_every < 0) return bad("mass_every must be >= 0");
+    if (p->checkpoint_every < 0) return bad("checkpoint_every must be >= 0");
     return LBPF_OK;
 }
 
@@ -401,6 +369,7 @@ void free_all(lbpf_ctx* ctx) {
     ctx->d_tile_inst = nullptr;
     if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
     ctx->graph = nullptr;
+    free_adjoint(ctx);
 }
 
 // One coupled step (both kernels), followed by the mass correction when it is due.
@@ -420,13 +389,22 @@ void launch_one_step(lbpf_ctx* ctx) {
     ctx->step += 1;
 }
 
-lbpf_status check_launch(lbpf_ctx* ctx, const char* what);
-
 // nsteps steps, replaying two-step CUDA graphs where possible: on a non-default
 // stream, when every step has the same kernels (mass correction off or every
 // step).  The graph is captured once per context; if capture fails the steps
 // are launched one by one.
 lbpf_status run_steps(lbpf_ctx* ctx, int64_t nsteps) {
+    if (ctx->p.checkpoint_every > 0 && !ctx->is_batch) {
+        // adjoint recording: a checkpoint after every k-th step, no graphs
+        for (int64_t s = 0; s < nsteps; ++s) {
+            launch_one_step(ctx);
+            if (ctx->step % ctx->p.checkpoint_every == 0) {
+                lbpf_status st = record_checkpoint(ctx);
+                if (st != LBPF_OK) return st;
+            }
+        }
+        return check_launch(ctx, "step kernels");
+    }
     const bool graphable = ctx->stream != nullptr && !ctx->graph_failed &&
                            (ctx->p.mass_every <= 1 || ctx->is_batch) && nsteps >= 4;
     if (!graphable) {
@@ -470,30 +448,6 @@ long long corr_stride_for(long long N) {
     for (long long p : primes)
         if (N % p != 0) return p % N == 0 ? 1 : p;
     return 1;
-}
-
-lbpf_status alloc(lbpf_ctx* ctx, void** ptr, size_t bytes, const char* what) {
-    if (const char* f = getenv("LBPF_FAULT")) {
-        if (strcmp(f, "alloc") == 0) return fail(ctx, LBPF_ENOMEM, std::string("injected allocation failure: ") + what);
-    }
-    cudaError_t e = cudaMalloc(ptr, bytes);
-    if (e != cudaSuccess) {
-        *ptr = nullptr;
-        cudaGetLastError();
-        return cuda_fail(ctx, e, what);
-    }
-    return LBPF_OK;
-}
-
-lbpf_status ensure_staging(lbpf_ctx* ctx) {
-    if (ctx->staging) return LBPF_OK;
-    return alloc(ctx, (void**)&ctx->staging, sizeof(double) * 3 * (size_t)ctx->sp.N, "staging");
-}
-
-lbpf_status check_launch(lbpf_ctx* ctx, const char* what) {
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(ctx, e, what);
-    return LBPF_OK;
 }
 
 template <typename R>
@@ -548,6 +502,11 @@ lbpf_status lbpf_create(const lbpf_params* p, const double* phi0, const double* 
     if (validate(p, why) != LBPF_OK) return fail(nullptr, LBPF_EINVAL, why);
     const Dispatch* ops = pick(p->lattice, p->precision);
     if (!ops) return fail(nullptr, LBPF_EUNSUPPORTED, "lattice/precision not built");
+    const AdjDispatch* aops = nullptr;
+    if (p->checkpoint_every > 0) {
+        aops = pick_adjoint(p->lattice, p->precision);
+        if (!aops) return fail(nullptr, LBPF_EUNSUPPORTED, "the adjoint is built for FP64 and FP32 storage only");
+    }
 
     lbpf_ctx* ctx = new (std::nothrow) lbpf_ctx();
     if (!ctx) return fail(nullptr, LBPF_ENOMEM, "host allocation failed");
@@ -556,6 +515,7 @@ lbpf_status lbpf_create(const lbpf_params* p, const double* phi0, const double* 
     ctx->q = p->lattice == LBPF_D3Q19 ? 19 : 9;
     ctx->kp = make_kparams(p);
     ctx->ops = ops;
+    ctx->aops = aops;
     ctx->stream = (cudaStream_t)cuda_stream;
     ctx->real_size = p->precision == LBPF_FP64 ? 8 : 4;
     ctx->store_size = p->precision == LBPF_FP64 ? 8 : (p->precision == LBPF_FP32 ? 4 : 2);
@@ -622,6 +582,7 @@ lbpf_status lbpf_create(const lbpf_params* p, const double* phi0, const double* 
         if (e != cudaSuccess) { cuda_fail(ctx, e, "mass-correction target"); return abort_create(LBPF_ECUDA); }
         if ((st = check_launch(ctx, "population mass kernels")) != LBPF_OK) return abort_create(st);
     }
+    if (aops && (st = record_checkpoint(ctx)) != LBPF_OK) return abort_create(st);
     e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) { cuda_fail(ctx, e, "initialisation"); return abort_create(LBPF_ECUDA); }
     *out = ctx;
@@ -661,6 +622,15 @@ lbpf_status lbpf_step_timed(lbpf_ctx* ctx, int64_t nsteps, double* kernel_ms) {
             cudaEventRecord(ev[4 * s + 3], ctx->stream);
             ctx->cur ^= 1;
             ctx->step += 1;
+            if (!ctx->is_batch && ctx->p.checkpoint_every > 0 && ctx->step % ctx->p.checkpoint_every == 0) {
+                st = record_checkpoint(ctx);
+                if (st != LBPF_OK) break;
+            }
+        }
+        if (st != LBPF_OK) {
+            cudaStreamSynchronize(ctx->stream);
+            for (auto& x : ev) if (x) cudaEventDestroy(x);
+            return st;
         }
         st = check_launch(ctx, "step kernels");
         cudaError_t e = cudaStreamSynchronize(ctx->stream);
@@ -781,6 +751,7 @@ lbpf_status lbpf_create_batch(const lbpf_params* p, int32_t n, const double* con
         if (p[i].lattice != LBPF_D2Q9) return fail(nullptr, LBPF_EUNSUPPORTED, "batches hold 2-D D2Q9 instances");
         if (p[i].precision != p[0].precision) return fail(nullptr, LBPF_EINVAL, "all instances need one precision");
         if (p[i].mass_every != 0) return fail(nullptr, LBPF_EUNSUPPORTED, "mass correction is not built for batches");
+        if (p[i].checkpoint_every != 0) return fail(nullptr, LBPF_EUNSUPPORTED, "the adjoint is not built for batches");
     }
     const BatchDispatch* bops = pick_batch(p[0].precision);
     if (!bops) return fail(nullptr, LBPF_EUNSUPPORTED, "precision not built");

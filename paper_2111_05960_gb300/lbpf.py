@@ -43,7 +43,7 @@ class lbpf_params(ctypes.Structure):
                 ("mu_eq", ctypes.c_double), ("counter_term", ctypes.c_int32),
                 ("anti_trapping", ctypes.c_int32), ("a_at", ctypes.c_double),
                 ("eps_n", ctypes.c_double), ("mass_every", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("checkpoint_every", ctypes.c_int32)]
 
 
 _lib = None
@@ -80,6 +80,7 @@ def load() -> ctypes.CDLL:
                               ctypes.POINTER(_vp), ctypes.c_int32, _vp, ctypes.POINTER(_vp)],
         "lbpf_batch_get_fields": [_vp, ctypes.c_int32, _vp, _vp, _vp, ctypes.c_int32],
         "lbpf_batch_solute_mass": [_vp, _dp],
+        "lbpf_adjoint_step": [_vp, _vp, _vp, _vp, _vp, ctypes.c_int32, _dp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -96,7 +97,8 @@ def exported_symbols():
     return ["lbpf_default_params", "lbpf_create", "lbpf_step", "lbpf_step_timed", "lbpf_mass",
             "lbpf_get_fields", "lbpf_get_populations", "lbpf_get_step", "lbpf_destroy",
             "lbpf_last_error", "lbpf_lattice_info", "lbpf_mass_noalloc", "lbpf_solute_mass",
-            "lbpf_create_batch", "lbpf_batch_get_fields", "lbpf_batch_solute_mass"]
+            "lbpf_create_batch", "lbpf_batch_get_fields", "lbpf_batch_solute_mass",
+            "lbpf_adjoint_step"]
 
 
 def _check(status: int, ctx=None):
@@ -217,6 +219,20 @@ def lbpf_mass_noalloc(c_dev, phi_dev, n: int, precision: int, out_dev, cuda_stre
     _check(load().lbpf_mass_noalloc(cp, pp, int(n), int(precision), op, cuda_stream or None))
 
 
+ADJ_PARAM_NAMES = ("D_l", "tau_g", "tau_h", "lam", "a_at", "D_s")
+
+
+def lbpf_adjoint_step(ctx, dL_dphi=None, dL_dc=None, dL_dphi0=None, dL_dc0=None,
+                      ptr_is_device: int = 0) -> np.ndarray:
+    """Reverse sweep over the trajectory since creation (see include/lbpf.h).
+    Writes dL/dphi0, dL/dc0 into the given arrays (either may be None) and
+    returns the parameter adjoints, ordered as ADJ_PARAM_NAMES."""
+    out = np.zeros(len(ADJ_PARAM_NAMES))
+    _check(load().lbpf_adjoint_step(ctx, _ptr(dL_dphi)[0], _ptr(dL_dc)[0], _ptr(dL_dphi0)[0],
+                                    _ptr(dL_dc0)[0], int(ptr_is_device), out.ctypes.data_as(_dp)), ctx)
+    return out
+
+
 def lbpf_lattice_info(lattice: int):
     q = ctypes.c_int32()
     e = (ctypes.c_int32 * 57)()
@@ -228,7 +244,7 @@ def lbpf_lattice_info(lattice: int):
 
 # ---- convenience wrapper -------------------------------------------------------------
 
-def params_from(model, precision="fp64", dx=1.0, dt=1.0, mass_every=0) -> lbpf_params:
+def params_from(model, precision="fp64", dx=1.0, dt=1.0, mass_every=0, checkpoint_every=0) -> lbpf_params:
     """lbpf_params from a workloads.ModelParams (lattice units unless dx, dt given)."""
     p = lbpf_default_params()
     p.nx, p.ny, p.nz = model.nx, model.ny, model.nz
@@ -243,6 +259,7 @@ def params_from(model, precision="fp64", dx=1.0, dt=1.0, mass_every=0) -> lbpf_p
     p.counter_term, p.anti_trapping = int(model.counter_term), int(model.anti_trapping)
     p.a_at, p.eps_n = model.a_at, model.eps_n
     p.mass_every = int(mass_every)
+    p.checkpoint_every = int(checkpoint_every)
     return p
 
 
@@ -250,9 +267,10 @@ class Simulation:
     """One GPU simulation context.  Host fields in/out are numpy float64 arrays
     shaped (nz, ny, nx); device fields are CUDA float64 tensors."""
 
-    def __init__(self, model, phi0, c0, precision="fp64", stream=None, lattice=None, mass_every=0):
+    def __init__(self, model, phi0, c0, precision="fp64", stream=None, lattice=None, mass_every=0,
+                 checkpoint_every=0):
         self.model = model
-        self.params = params_from(model, precision, mass_every=mass_every)
+        self.params = params_from(model, precision, mass_every=mass_every, checkpoint_every=checkpoint_every)
         if lattice is not None:
             self.params.lattice = int(lattice)
         is_dev = hasattr(phi0, "data_ptr")
@@ -280,6 +298,14 @@ class Simulation:
         phi, c, mu = (np.empty(self.shape) for _ in range(3))
         lbpf_get_fields(self.ctx, phi, c, mu, 0)
         return phi, c, mu
+
+    def adjoint(self, dL_dphi=None, dL_dc=None):
+        """(dL/dphi0, dL/dc0, parameter adjoints) of a loss of the current fields;
+        needs checkpoint_every > 0 at construction."""
+        as_np = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64).reshape(self.shape)
+        dphi0, dc0 = np.empty(self.shape), np.empty(self.shape)
+        pv = lbpf_adjoint_step(self.ctx, as_np(dL_dphi), as_np(dL_dc), dphi0, dc0, 0)
+        return dphi0, dc0, pv
 
     def populations(self):
         g = np.empty((self.q,) + self.shape)

@@ -141,7 +141,8 @@ def grf_mask(shape, corr=8.0, porosity=0.35, seed=0) -> np.ndarray:
         k2 = kx * kx + ky * ky
         field_k = np.fft.rfftn(noise)
         k2 = k2[..., : field_k.shape[-1]]
-    smooth = np.fft.irfftn(field_k * np.exp(-2.0 * math.pi ** 2 * corr ** 2 * k2), s=shape)
+    smooth = np.fft.irfftn(field_k * np.exp(-2.0 * math.pi ** 2 * corr ** 2 * k2), s=shape,
+                           axes=tuple(range(len(shape))))
     thr = np.quantile(smooth, porosity)
     return smooth < thr
 
@@ -174,6 +175,22 @@ def porous_3d(n=256, porosity=0.35, seed=0, W=3.0, D_l=0.1, D_s=0.0, c_solid=1.0
     c = blend(phi, c_solid, c_liquid)
     p = recipe(n, n, nz, D_l=D_l, D_s=D_s, W=W, counter_term=counter_term)
     return p, phi, c
+
+
+def differentiable_3d(n=128, porosity=0.4, seed=2, eps_n=1e-3):
+    """The differentiable 3-D workload: the porous medium of porous_3d, a seeded
+    per-z-slab solid-fraction target U[0.4, 0.7] for the loss
+    L = sum_z (mean_xy phi_T - target_z)^2, and the normal regularised with
+    eps_n = 1e-3.  With eps_n = 1e-12 the step's Jacobian is ~ phi(1 - phi)/eps_n
+    at nodes where grad phi vanishes inside a thin neck or gap (the counter term
+    turns n freely there), so adjoints through such media reach 1e5..1e25 and no
+    finite difference can follow them; eps_n = 1e-3 leaves interfaces
+    (|grad phi| ~ 0.1) unchanged to ~1e-4 and bounds that factor."""
+    p, phi, c = porous_3d(n, porosity=porosity, seed=seed)
+    p = replace(p, eps_n=eps_n)
+    rng = np.random.Generator(np.random.PCG64(seed + 1000))
+    target = rng.uniform(0.4, 0.7, p.nz)
+    return p, phi, c, target
 
 
 # ---- batch of 2-D instances ------------------------------------------------

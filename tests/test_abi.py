@@ -84,6 +84,7 @@ def test_default_params(lib):
     (lambda p: (p.bc.__setitem__(0, 1), setattr(p, "nx", 1)), "bounce-back axis"),
     (lambda p: p.bc.__setitem__(1, 3), "unknown boundary"),
     (lambda p: setattr(p, "lambda_", float("nan")), "non-finite"),
+    (lambda p: setattr(p, "checkpoint_every", -1), "checkpoint_every"),
 ])
 def test_create_rejects_bad_parameters_without_a_gpu(lib, mutate, msg):
     p = L.lbpf_default_params()
@@ -131,3 +132,23 @@ def test_create_batch_validates_on_the_host(lib):
     with pytest.raises(L.LbpfError) as ei:
         L.lbpf_create_batch([good, bad], [a, a], [a, a])
     assert ei.value.status == L.LBPF_EINVAL and "instance 1" in str(ei.value)
+
+
+def test_adjoint_arguments_are_checked_on_the_host(lib):
+    out = np.zeros(len(L.ADJ_PARAM_NAMES))
+    assert lib.lbpf_adjoint_step(None, None, None, None, None, 0,
+                                 out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == L.LBPF_EINVAL
+    for prec in (L.LBPF_FP32_BF16DEV, L.LBPF_FP32_FP16DEV):
+        p = L.lbpf_default_params()
+        p.precision, p.checkpoint_every = prec, 10
+        a = np.zeros(64 * 64)
+        with pytest.raises(L.LbpfError) as ei:
+            L.lbpf_create(p, a, a, 0)
+        assert ei.value.status == L.LBPF_EUNSUPPORTED and "adjoint" in str(ei.value)
+    good = L.lbpf_default_params()
+    bad = L.lbpf_default_params()
+    bad.checkpoint_every = 5
+    a = np.zeros(64 * 64)
+    with pytest.raises(L.LbpfError) as ei:
+        L.lbpf_create_batch([good, bad], [a, a], [a, a])
+    assert ei.value.status == L.LBPF_EUNSUPPORTED
