@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=20, help="steps of the FP64 comparison run")
+    ap.add_argument("--adj-steps", type=int, default=2000, help="steps of the 128^3 adjoint run (0 = skip)")
+    ap.add_argument("--adj-every", type=int, default=100, help="checkpoint interval of the adjoint run")
     ap.add_argument("--batch-steps", type=int, default=40,
                     help="timed steps of the 384-instance 2-D batch (0 = skip)")
     return ap.parse_args()
@@ -175,6 +177,65 @@ def batch_measurement(args, stream, hbm):
             "ms_per_step": ms, "mlups": nodes / (ms * 1e-3) / 1e6, "bytes_per_node": bytes_node,
             "achieved_gbs": gbs, "frac": gbs / hbm, "launch": "2 persistent launches per step, CUDA graph",
             "kernel_ms": {"k_batch_phi": k_phi / 10, "k_batch_c": k_c / 10}}
+
+
+# Algorithmic bytes per node of one reversed step (FP32, D3Q19): k_adj_h reads h,
+# gathers hb and writes hb (3 x 76), reads phi, c, phi^{n+1}, cb (16) and writes
+# ten work values (40); k_adj_g reads g, gathers gb, writes gb (228), reads phi,
+# c, phib, dphi-bar, n-bar, mu-bar (32) and updates grad-bar, phi-bar, c-bar
+# (40); k_adj_finish reads phi-bar, grad-bar, c-bar (20) and writes two fields (8).
+ADJ_BYTES_PER_NODE_FP32 = 284 + 300 + 28
+
+
+def adjoint_measurement(args, stream, hbm, fwd_bytes_per_node):
+    """The differentiable 3-D workload: 128^3 porous medium (porosity 0.4), FP32
+    with the FP64 mass correction, T steps recorded every k, the slab
+    solid-fraction loss.  Times the forward steps and the whole reverse sweep
+    (checkpoint restores, segment replays and three adjoint kernels per step)
+    with CUDA events on the context's stream; seed and outputs stay on the GPU."""
+    import torch
+    from paper_2111_05960_gb300 import lbpf as L
+    from paper_2111_05960_gb300 import workloads as WL
+    m, phi0, c0, target = WL.differentiable_3d(128)
+    N, T, K = m.nodes, args.adj_steps, args.adj_every
+    sim = L.Simulation(m, phi0, c0, precision="fp32", stream=stream.cuda_stream, mass_every=1,
+                       checkpoint_every=K)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    sim.step(T)
+    ev[1].record(stream)
+    phi = torch.empty(m.shape, dtype=torch.float64, device="cuda")
+    L.lbpf_get_fields(sim.ctx, phi, None, None, 1)
+    with torch.cuda.stream(stream):
+        frac = phi.mean(dim=(1, 2))
+        tgt = torch.tensor(target, dtype=torch.float64, device="cuda")
+        loss = float(((frac - tgt) ** 2).sum())
+        seed = (2.0 * (frac - tgt) / (m.nx * m.ny))[:, None, None].expand(m.shape).contiguous()
+        dphi0 = torch.empty_like(phi)
+        dc0 = torch.empty_like(phi)
+    torch.cuda.synchronize()
+    ev[2].record(stream)
+    pv = L.lbpf_adjoint_step(sim.ctx, seed, None, dphi0, dc0, 1)
+    ev[3].record(stream)
+    torch.cuda.synchronize()
+    sim.close()
+    fwd_ms = ev[0].elapsed_time(ev[1]) / T
+    sweep_ms = ev[2].elapsed_time(ev[3]) / T
+    rev_ms = max(sweep_ms - fwd_ms, 1e-9)        # the replay runs the forward kernels again
+    gbs = ADJ_BYTES_PER_NODE_FP32 * N / (rev_ms * 1e-3) / 1e9
+    return {"workload": "differentiable_3d_128_d3q19_fp32", "nodes": N, "steps": T, "checkpoint_every": K,
+            "loss": loss, "forward_ms_per_step": fwd_ms, "adjoint_sweep_ms_per_step": sweep_ms,
+            "adjoint_to_forward": sweep_ms / fwd_ms,
+            "reverse_kernels_ms_per_step": rev_ms,
+            "reverse_bytes_per_node": ADJ_BYTES_PER_NODE_FP32,
+            "reverse_achieved_gbs": gbs, "reverse_frac": gbs / hbm,
+            "ideal_adjoint_to_forward": (ADJ_BYTES_PER_NODE_FP32 + fwd_bytes_per_node) / fwd_bytes_per_node,
+            "dL_dparams": dict(zip(L.ADJ_PARAM_NAMES, [float(v) for v in pv])),
+            "dL_dM_phi": 3.0 * float(pv[1]),
+            "max_abs_dL_dphi0": float(dphi0.abs().max()),
+            "note": "sweep = checkpoint restores + replay of every segment + reverse kernels; "
+                    "reverse kernels = sweep - forward (the replay is the forward's kernels)"}
 
 
 def cpu_baseline(model, phi0, c0, budget_s=12.0):
@@ -325,6 +386,17 @@ def run_ours(args):
         except Exception as ex:   # reported, never silently dropped
             batch = {"error": str(ex)}
 
+    adj = None
+    if args.adj_steps > 0 and prec == "fp32":
+        try:
+            adj = adjoint_measurement(args, stream, hbm, b_phi + b_c)
+            if "fp64_forward" in extra:
+                # per node: the sweep runs on 128^3, the FP64 forward on the main grid
+                adj["adjoint_to_fp64_forward_per_node"] = (adj["adjoint_sweep_ms_per_step"] / adj["nodes"]) / \
+                    (extra["fp64_forward"]["ms_per_step"] / N)
+        except Exception as ex:   # reported, never silently dropped
+            adj = {"error": str(ex)}
+
     e2e = None
     if not args.no_e2e:
         # end to end through the public API with host buffers: create from pinned host
@@ -373,7 +445,7 @@ def run_ours(args):
                           "parallelism": "replicas" if world > 1 else "single GPU",
                           "l2": "state %.1f GB per buffer set, larger than L2 (no flush needed)"
                                 % (N * (2 * q * store + 2 * real) / 1e9)},
-               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "batch_2d": batch,
+               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "batch_2d": batch, "adjoint": adj,
                "gpu_launches": (4 if mass_every else 2) * args.steps, "clocks": clk,
                "mass": {"solute_before": m_before, "solute_after": m_after,
                         "relative_drift": (m_after - m_before) / m_before,

@@ -27,14 +27,23 @@ struct AdjBufs {
     void* hb[2];
     void* phib[2];
     void* cb[2];
-    void* work;          // 10 N values (AdjWork)
+    void* work;          // 6 N values (AdjWork)
     double* blockacc;    // kAdjParams x nblk
     double* pout;        // kAdjParams
     MassCorr* corr;
     int nblk;
 };
 
-int adj_blocks(const lbpf_ctx* ctx) { return (int)((ctx->sp.N + kAdjThreads - 1) / kAdjThreads); }
+// 32 x 8 tiles of each z-plane; planes beyond the grid's z extent loop
+dim3 adj_grid(const lbpf_ctx* ctx) {
+    const StepParams& P = ctx->sp;
+    return dim3((P.nx + kAdjBX - 1) / kAdjBX, (P.ny + kAdjBY - 1) / kAdjBY, std::min(P.nz, 32768));
+}
+
+int adj_blocks(const lbpf_ctx* ctx) {
+    const dim3 g = adj_grid(ctx);
+    return (int)(g.x * g.y * g.z);
+}
 
 size_t adj_layout(const lbpf_ctx* ctx, void* base, AdjBufs* a) {
     const size_t N = (size_t)ctx->sp.N, rs = ctx->real_size;
@@ -47,7 +56,7 @@ size_t adj_layout(const lbpf_ctx* ctx, void* base, AdjBufs* a) {
     for (int i = 0; i < 2; ++i) v.hb[i] = take(rs * ctx->q * N);
     for (int i = 0; i < 2; ++i) v.phib[i] = take(rs * N);
     for (int i = 0; i < 2; ++i) v.cb[i] = take(rs * N);
-    v.work = take(rs * 10 * N);
+    v.work = take(rs * 6 * N);
     v.blockacc = (double*)take(sizeof(double) * kAdjParams * nblk);
     v.pout = (double*)take(sizeof(double) * kAdjParams);
     v.corr = (MassCorr*)take(sizeof(MassCorr));
@@ -74,35 +83,36 @@ struct AdjImpl {
         R* w = (R*)base;
         AdjWork<R> T;
         T.phi = w;
-        T.mu = w + N;
-        T.c = w + 2 * N;
-        T.dphi = w + 3 * N;
-        T.grad = w + 4 * N;
-        T.n = w + 7 * N;
+        T.c = w + N;
+        T.dphi = w + 2 * N;
+        T.grad = w + 3 * N;
         return T;
     }
     // adjoint of the step from state s (phi1 = phi of the next state)
     static void step(lbpf_ctx* ctx, const StateView& s, const void* phi1, const AdjBufs& a, int cur) {
         const int nxt = cur ^ 1;
         const AdjWork<R> T = work(ctx, a.work);
-        const unsigned nb = (unsigned)a.nblk;
-        k_adj_h<L, R><<<nb, kAdjThreads, 0, ctx->stream>>>(
-            ctx->kp, (const R*)s.h, (const R*)s.phi, (const R*)s.c, (const R*)phi1, (const R*)a.hb[cur],
+        const dim3 grid = adj_grid(ctx), block(kAdjBX, kAdjBY);
+        const AdjCoef<R> C = make_adj_coef<R>(ctx->sp);
+        k_adj_h<L, R><<<grid, block, 0, ctx->stream>>>(
+            ctx->sp, C, (const R*)s.h, (const R*)s.phi, (const R*)s.c, (const R*)phi1, (const R*)a.hb[cur],
             (const R*)a.cb[cur], (R*)a.hb[nxt], T, a.blockacc, a.nblk);
-        k_adj_g<L, R><<<nb, kAdjThreads, 0, ctx->stream>>>(
-            ctx->kp, (const R*)s.g, (const R*)s.phi, (const R*)s.c, (const R*)a.gb[cur], (const R*)a.phib[cur],
-            (R*)a.gb[nxt], T, a.blockacc, a.nblk);
-        k_adj_finish<L, R><<<nb, kAdjThreads, 0, ctx->stream>>>(ctx->kp, T, (R*)a.phib[nxt], (R*)a.cb[nxt]);
+        k_adj_g<L, R><<<grid, block, 0, ctx->stream>>>(
+            ctx->sp, C, (const R*)s.g, (const R*)s.phi, (const R*)s.c, (const R*)a.gb[cur], (const R*)a.phib[cur],
+            (R*)a.gb[nxt], T, (R*)a.phib[nxt], (R*)a.cb[nxt], a.blockacc, a.nblk);
+        k_adj_finish<L, R><<<grid, block, 0, ctx->stream>>>(ctx->sp, T.grad, (R*)a.phib[nxt]);
     }
     // adjoint of the initialisation from the initial fields of state s
     static void init(lbpf_ctx* ctx, const StateView& s, const AdjBufs& a, int cur) {
         const int nxt = cur ^ 1;
         const AdjWork<R> T = work(ctx, a.work);
-        const unsigned nb = (unsigned)a.nblk;
-        k_adj_init<L, R><<<nb, kAdjThreads, 0, ctx->stream>>>(
-            ctx->kp, (const R*)s.phi, (const R*)s.c, (const R*)a.gb[cur], (const R*)a.hb[cur],
-            (const R*)a.phib[cur], (const R*)a.cb[cur], T, a.blockacc, a.nblk);
-        k_adj_finish<L, R><<<nb, kAdjThreads, 0, ctx->stream>>>(ctx->kp, T, (R*)a.phib[nxt], (R*)a.cb[nxt]);
+        const dim3 grid = adj_grid(ctx), block(kAdjBX, kAdjBY);
+        const AdjCoef<R> C = make_adj_coef<R>(ctx->sp);
+        k_adj_init<L, R><<<grid, block, 0, ctx->stream>>>(
+            ctx->sp, C, (const R*)s.phi, (const R*)s.c, (const R*)a.gb[cur], (const R*)a.hb[cur],
+            (const R*)a.phib[cur], (const R*)a.cb[cur], T.grad, (R*)a.phib[nxt], (R*)a.cb[nxt], a.blockacc,
+            a.nblk);
+        k_adj_finish<L, R><<<grid, block, 0, ctx->stream>>>(ctx->sp, T.grad, (R*)a.phib[nxt]);
     }
     static void from_f64(lbpf_ctx* ctx, const double* src, void* dst) {
         const long long N = ctx->sp.N;

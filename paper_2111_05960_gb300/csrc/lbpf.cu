@@ -506,6 +506,7 @@ lbpf_status lbpf_create(const lbpf_params* p, const double* phi0, const double* 
     if (p->checkpoint_every > 0) {
         aops = pick_adjoint(p->lattice, p->precision);
         if (!aops) return fail(nullptr, LBPF_EUNSUPPORTED, "the adjoint is built for FP64 and FP32 storage only");
+        if (p->ny > 8 * 65535) return fail(nullptr, LBPF_EUNSUPPORTED, "the adjoint needs ny <= 524280");
     }
 
     lbpf_ctx* ctx = new (std::nothrow) lbpf_ctx();
