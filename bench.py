@@ -180,17 +180,18 @@ def batch_measurement(args, stream, hbm):
 
 
 # Algorithmic bytes per node of one reversed step (FP32, D3Q19): k_adj_h reads h,
-# gathers hb and writes hb (3 x 76), reads phi, c, phi^{n+1}, cb (16) and writes
-# ten work values (40); k_adj_g reads g, gathers gb, writes gb (228), reads phi,
-# c, phib, dphi-bar, n-bar, mu-bar (32) and updates grad-bar, phi-bar, c-bar
-# (40); k_adj_finish reads phi-bar, grad-bar, c-bar (20) and writes two fields (8).
-ADJ_BYTES_PER_NODE_FP32 = 284 + 300 + 28
+# gathers hb and writes hb (3 x 76), reads phi, c, phi^{n+1}, cb, phib (20) and
+# writes seven work values (28); k_adj_g reads g, gathers gb, writes gb (228),
+# reads phi, c and five work values (28), updates the grad adjoint (24) and
+# writes the phi and c adjoints (8); k_adj_finish reads the grad adjoint (12)
+# and updates the phi adjoint (8).
+ADJ_BYTES_PER_NODE_FP32 = 276 + 288 + 20
 
 
 def adjoint_measurement(args, stream, hbm, fwd_bytes_per_node):
     """The differentiable 3-D workload: 128^3 porous medium (porosity 0.4), FP32
     with the FP64 mass correction, T steps recorded every k, the slab
-    solid-fraction loss.  Times the forward steps and the whole reverse sweep
+    solid-fraction loss (workloads.slab_loss).  Times the forward steps and the whole reverse sweep
     (checkpoint restores, segment replays and three adjoint kernels per step)
     with CUDA events on the context's stream; seed and outputs stay on the GPU."""
     import torch
@@ -208,10 +209,7 @@ def adjoint_measurement(args, stream, hbm, fwd_bytes_per_node):
     phi = torch.empty(m.shape, dtype=torch.float64, device="cuda")
     L.lbpf_get_fields(sim.ctx, phi, None, None, 1)
     with torch.cuda.stream(stream):
-        frac = phi.mean(dim=(1, 2))
-        tgt = torch.tensor(target, dtype=torch.float64, device="cuda")
-        loss = float(((frac - tgt) ** 2).sum())
-        seed = (2.0 * (frac - tgt) / (m.nx * m.ny))[:, None, None].expand(m.shape).contiguous()
+        loss, seed = WL.slab_loss(phi, torch.tensor(target, dtype=torch.float64, device="cuda"))
         dphi0 = torch.empty_like(phi)
         dc0 = torch.empty_like(phi)
     torch.cuda.synchronize()

@@ -27,7 +27,7 @@ struct AdjBufs {
     void* hb[2];
     void* phib[2];
     void* cb[2];
-    void* work;          // 6 N values (AdjWork)
+    void* work;          // 7 N values (AdjWork)
     double* blockacc;    // kAdjParams x nblk
     double* pout;        // kAdjParams
     MassCorr* corr;
@@ -56,7 +56,7 @@ size_t adj_layout(const lbpf_ctx* ctx, void* base, AdjBufs* a) {
     for (int i = 0; i < 2; ++i) v.hb[i] = take(rs * ctx->q * N);
     for (int i = 0; i < 2; ++i) v.phib[i] = take(rs * N);
     for (int i = 0; i < 2; ++i) v.cb[i] = take(rs * N);
-    v.work = take(rs * 6 * N);
+    v.work = take(rs * 7 * N);
     v.blockacc = (double*)take(sizeof(double) * kAdjParams * nblk);
     v.pout = (double*)take(sizeof(double) * kAdjParams);
     v.corr = (MassCorr*)take(sizeof(MassCorr));
@@ -85,7 +85,8 @@ struct AdjImpl {
         T.phi = w;
         T.c = w + N;
         T.dphi = w + 2 * N;
-        T.grad = w + 3 * N;
+        T.pt = w + 3 * N;
+        T.grad = w + 4 * N;
         return T;
     }
     // adjoint of the step from state s (phi1 = phi of the next state)
@@ -96,10 +97,10 @@ struct AdjImpl {
         const AdjCoef<R> C = make_adj_coef<R>(ctx->sp);
         k_adj_h<L, R><<<grid, block, 0, ctx->stream>>>(
             ctx->sp, C, (const R*)s.h, (const R*)s.phi, (const R*)s.c, (const R*)phi1, (const R*)a.hb[cur],
-            (const R*)a.cb[cur], (R*)a.hb[nxt], T, a.blockacc, a.nblk);
+            (const R*)a.cb[cur], (const R*)a.phib[cur], (R*)a.hb[nxt], T, a.blockacc, a.nblk);
         k_adj_g<L, R><<<grid, block, 0, ctx->stream>>>(
-            ctx->sp, C, (const R*)s.g, (const R*)s.phi, (const R*)s.c, (const R*)a.gb[cur], (const R*)a.phib[cur],
-            (R*)a.gb[nxt], T, (R*)a.phib[nxt], (R*)a.cb[nxt], a.blockacc, a.nblk);
+            ctx->sp, C, (const R*)s.g, (const R*)s.phi, (const R*)s.c, (const R*)a.gb[cur], (R*)a.gb[nxt], T,
+            (R*)a.phib[nxt], (R*)a.cb[nxt], a.blockacc, a.nblk);
         k_adj_finish<L, R><<<grid, block, 0, ctx->stream>>>(ctx->sp, T.grad, (R*)a.phib[nxt]);
     }
     // adjoint of the initialisation from the initial fields of state s

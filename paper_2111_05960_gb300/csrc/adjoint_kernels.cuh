@@ -41,6 +41,7 @@ struct AdjWork {        // per-node partial adjoints, SoA, N entries each
     R* phi;             // phi (local terms of the composition part)
     R* c;               // c
     R* dphi;            // dphi/dt = phi^{n+1} - phi^n
+    R* pt;              // phi^{n+1}: the incoming phi adjoint plus that of dphi/dt
     R* grad;            // grad phi, [3][N]
 };
 
@@ -332,7 +333,8 @@ template <class L, typename R>
 __global__ void __launch_bounds__(kAdjThreads, adj_minb<R>())
 k_adj_h(const StepParams P, const AdjCoef<R> C, const R* __restrict__ h, const R* __restrict__ phi,
         const R* __restrict__ c, const R* __restrict__ phi1, const R* __restrict__ hb_in,
-        const R* __restrict__ cb_in, R* __restrict__ hb_out, AdjWork<R> T, double* __restrict__ pacc, int nblk) {
+        const R* __restrict__ cb_in, const R* __restrict__ phib_in, R* __restrict__ hb_out, AdjWork<R> T,
+        double* __restrict__ pacc, int nblk) {
     const long long N = P.N;
     R pv[kAdjParams] = {R(0), R(0), R(0), R(0), R(0), R(0)};
     const int x = blockIdx.x * kAdjBX + threadIdx.x, y = blockIdx.y * kAdjBY + threadIdx.y;
@@ -376,6 +378,7 @@ k_adj_h(const StepParams P, const AdjCoef<R> C, const R* __restrict__ h, const R
         T.phi[i] = phib;
         T.c[i] = cb;
         T.dphi[i] = dphib;
+        T.pt[i] = phib_in[i] + dphib;
         for (int d = 0; d < 3; ++d) T.grad[d * N + i] = gradb[d];
     }
     adj_param_flush(pv, pacc, nblk);
@@ -385,8 +388,8 @@ k_adj_h(const StepParams P, const AdjCoef<R> C, const R* __restrict__ h, const R
 template <class L, typename R>
 __global__ void __launch_bounds__(kAdjThreads, adj_minb<R>())
 k_adj_g(const StepParams P, const AdjCoef<R> C, const R* __restrict__ g, const R* __restrict__ phi,
-        const R* __restrict__ c, const R* __restrict__ gb_in, const R* __restrict__ phib_in, R* __restrict__ gb_out,
-        AdjWork<R> T, R* __restrict__ phib_out, R* __restrict__ cb_out, double* __restrict__ pacc, int nblk) {
+        const R* __restrict__ c, const R* __restrict__ gb_in, R* __restrict__ gb_out, AdjWork<R> T,
+        R* __restrict__ phib_out, R* __restrict__ cb_out, double* __restrict__ pacc, int nblk) {
     const long long N = P.N;
     R pv[kAdjParams] = {R(0), R(0), R(0), R(0), R(0), R(0)};
     const int x = blockIdx.x * kAdjBX + threadIdx.x, y = blockIdx.y * kAdjBY + threadIdx.y;
@@ -398,7 +401,7 @@ k_adj_g(const StepParams P, const AdjCoef<R> C, const R* __restrict__ g, const R
         PhiSource<L, R> src;
         src.compute(C, f);
         const R dphib_here = T.dphi[i];
-        const R pt = phib_in[i] + dphib_here;            // adjoint of phi^{n+1} at this node
+        const R pt = T.pt[i];                            // adjoint of phi^{n+1} at this node
         // s_k: adjoint of the post-collision population k; phi^{n+1} = sum g' + G/2
         R S0 = R(0), SV[3] = {R(0), R(0), R(0)}, Sneq = R(0);
 #pragma unroll
@@ -406,7 +409,7 @@ k_adj_g(const StepParams P, const AdjCoef<R> C, const R* __restrict__ g, const R
             const long long d = i + nbr_off<L>(a, k);
             const bool wall = (a.walls & out_bits<L>(k)) != 0;
             const R s = wall ? gb_in[(long long)L::opp(k) * N + i] + pt
-                             : gb_in[(long long)k * N + d] + phib_in[d] + T.dphi[d];
+                             : gb_in[(long long)k * N + d] + T.pt[d];
             gb_out[(long long)k * N + i] = (R(1) - C.omg) * s;
             Sneq += s * (R(L::w(k)) * f.ph - R(0.5) * src.G(C, f, k) - g[(long long)k * N + i]);
             S0 += R(L::w(k)) * s;

@@ -178,19 +178,35 @@ def porous_3d(n=256, porosity=0.35, seed=0, W=3.0, D_l=0.1, D_s=0.0, c_solid=1.0
 
 
 def differentiable_3d(n=128, porosity=0.4, seed=2, eps_n=1e-3):
-    """The differentiable 3-D workload: the porous medium of porous_3d, a seeded
-    per-z-slab solid-fraction target U[0.4, 0.7] for the loss
-    L = sum_z (mean_xy phi_T - target_z)^2, and the normal regularised with
-    eps_n = 1e-3.  With eps_n = 1e-12 the step's Jacobian is ~ phi(1 - phi)/eps_n
-    at nodes where grad phi vanishes inside a thin neck or gap (the counter term
-    turns n freely there), so adjoints through such media reach 1e5..1e25 and no
-    finite difference can follow them; eps_n = 1e-3 leaves interfaces
-    (|grad phi| ~ 0.1) unchanged to ~1e-4 and bounds that factor."""
+    """The differentiable 3-D workload: the porous medium of porous_3d with the
+    normal regularised by eps_n = 1e-3, and the seeded target of the slab
+    solid-fraction loss (slab_loss): s*_z = s_z(0) - 0.05 u_z, u ~ U[0, 1]
+    (PCG64 seed 3), s_z(0) the initial solid fraction of z-slab z.
+
+    With eps_n = 1e-12 the step's Jacobian is ~ phi(1 - phi)/eps_n at nodes where
+    grad phi vanishes inside a thin neck or gap (the counter term turns n freely
+    there), so adjoints through such media reach 1e5..1e25 and no finite
+    difference can follow them; eps_n = 1e-3 leaves interfaces (|grad phi| ~ 0.1)
+    unchanged to ~1e-4 and bounds that factor."""
     p, phi, c = porous_3d(n, porosity=porosity, seed=seed)
     p = replace(p, eps_n=eps_n)
-    rng = np.random.Generator(np.random.PCG64(seed + 1000))
-    target = rng.uniform(0.4, 0.7, p.nz)
-    return p, phi, c, target
+    s0 = (1.0 - phi).mean(axis=(1, 2))
+    u = np.random.Generator(np.random.PCG64(3)).uniform(0.0, 1.0, p.nz)
+    return p, phi, c, s0 - 0.05 * u
+
+
+def slab_loss(phi, target):
+    """L = sum_z (s_z - s*_z)^2 with s_z = mean_xy(1 - phi) the solid fraction of
+    z-slab z (phi = 0 is the solid), and dL/dphi.  phi: (nz, ny, nx); works on
+    numpy arrays and on torch tensors."""
+    nz, ny, nx = phi.shape
+    s = 1.0 - phi.mean(axis=(1, 2)) if isinstance(phi, np.ndarray) else 1.0 - phi.mean(dim=(1, 2))
+    r = s - target
+    loss = float((r * r).sum())
+    g = (-2.0 / (nx * ny)) * r
+    if isinstance(phi, np.ndarray):
+        return loss, np.broadcast_to(g[:, None, None], phi.shape).copy()
+    return loss, g[:, None, None].expand(phi.shape).contiguous()
 
 
 # ---- batch of 2-D instances ------------------------------------------------
