@@ -153,7 +153,8 @@ def algorithmic_bytes(q: int, real: int, store: int):
 def batch_measurement(args, stream, hbm):
     """The 384-instance 2-D sweep (sizes 64..768, 1-8 discs, random D_l and
     M_phi/D_l, counter term on or off), FP32, stepped as one batch: one
-    persistent launch per kernel phase, two steps per replayed CUDA graph."""
+    persistent launch per kernel phase over row-marched tiles whose shape the
+    library's autotuner picked at creation, two steps per replayed CUDA graph."""
     import torch
     from paper_2111_05960_gb300 import lbpf as L
     from paper_2111_05960_gb300 import workloads as WL
@@ -170,10 +171,12 @@ def batch_measurement(args, stream, hbm):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.batch_steps
     k_phi, k_c, _ = b.step_timed(10)
+    tile, tune_ms = b.tile()
     b.close()
     bytes_node = 2 * 9 * 4 + 2 * 4 + 2 * 9 * 4     # phi kernel 80 B, composition kernel 72 B
     gbs = bytes_node * nodes / (ms * 1e-3) / 1e9
     return {"workload": "batch_2d_384_d2q9_fp32", "instances": 384, "nodes": nodes, "steps": args.batch_steps,
+            "tile": {"shape": list(tile), "autotune_ms_per_step": dict(zip(["%dx%d" % t for t in L.BATCH_TILES], [float(v) for v in tune_ms]))},
             "ms_per_step": ms, "mlups": nodes / (ms * 1e-3) / 1e6, "bytes_per_node": bytes_node,
             "achieved_gbs": gbs, "frac": gbs / hbm, "launch": "2 persistent launches per step, CUDA graph",
             "kernel_ms": {"k_batch_phi": k_phi / 10, "k_batch_c": k_c / 10}}

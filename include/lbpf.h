@@ -192,6 +192,20 @@ lbpf_status lbpf_create_batch(const lbpf_params *p, int32_t n, const double *con
                               const double *const *c0, int32_t ptr_is_device, void *cuda_stream,
                               lbpf_ctx **out);
 
+/* Tile shape of a batch's step kernels: each persistent block walks tiles of
+ * *tile_x columns x *tile_rows rows (row segments marched along y).  At
+ * creation the library times one step with each built shape (64x16, 64x32,
+ * 128x16, 128x32, 256x16) on the batch itself and keeps the fastest; the shape
+ * changes the schedule only, never the results.  ms_per_step (optional, 5
+ * doubles) receives the timed milliseconds per step of each shape in that
+ * order.  Errors: EINVAL (NULL pointers, not a batch). */
+lbpf_status lbpf_batch_tile(const lbpf_ctx *ctx, int32_t *tile_x, int32_t *tile_rows, double *ms_per_step);
+
+/* Use one of the built tile shapes instead of the autotuned one.  Synchronises
+ * the stream.  Errors: EINVAL (not a batch, or a shape that is not built),
+ * ESTATE. */
+lbpf_status lbpf_batch_set_tile(lbpf_ctx *ctx, int32_t tile_x, int32_t tile_rows);
+
 /* Fields of instance i of a batch, as lbpf_get_fields (FP64 [ny][nx]). */
 lbpf_status lbpf_batch_get_fields(lbpf_ctx *ctx, int32_t i, double *phi, double *c, double *mu,
                                   int32_t ptr_is_device);

@@ -10,7 +10,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libgb_lbpf.so")
-SOURCES = ["lbpf.cu", "adjoint.cu", "noalloc.cu"]
+SOURCES = ["lbpf.cu", "batch.cu", "adjoint.cu", "noalloc.cu"]
 OBJDIR = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -4,11 +4,13 @@
 //
 // Every instance keeps its own SoA layout ([k][y][x] populations, [y][x]
 // fields) inside shared concatenated buffers.  The instances are cut into
-// 32 x 8 tiles; one flat list holds the tiles of all instances, and a
-// persistent grid (SMs x resident blocks) walks it round-robin, so the work is
-// balanced whatever the size mix.  A tile is processed by the same z-march code
-// as a single simulation (one plane), with its instance's parameters read from
-// a device table.
+// tiles of BX columns x ROWS rows; one flat list holds the tiles of all
+// instances, and a persistent grid (SMs x resident blocks) walks it
+// round-robin, so the work is balanced whatever the size mix.  A tile is
+// processed by the same row-marching code as a single 2-D simulation (the
+// D2Q9R view: BX-long row segments, ROWS rows), with its instance's parameters
+// read from a device table.  The tile shape is chosen per batch by timing the
+// candidates below on the batch itself.
 #pragma once
 
 #include "step_kernels.cuh"
@@ -17,42 +19,58 @@ namespace lbpf {
 
 struct BatchInst {
     KParams K;             // geometry, coefficients and link offsets of the instance
+    KParams Km;            // the same in the row-marching view ([ny][1][nx])
     long long pop_off;     // element offset of the instance's populations
     long long fld_off;     // element offset of the instance's fields
-    int tiles_x;           // 32-wide tiles along x
+    int tiles_x;           // tiles along x for the current tile shape
     int tile_begin;        // index of the instance's first tile in the flat list
     int walls;             // any bounce-back axis
     int pad;
 };
 
-constexpr int kBatchBY = 8;
+struct BatchTile {
+    int bx, rows;
+};
+// Candidate tile shapes (BX threads per block, 1024 / BX resident blocks).
+constexpr BatchTile kBatchTiles[] = {{64, 16}, {64, 32}, {128, 16}, {128, 32}, {256, 16}};
+constexpr int kNumBatchTiles = sizeof(kBatchTiles) / sizeof(kBatchTiles[0]);
 
-template <class SP, bool IS_PHI>
-__global__ void __launch_bounds__(32 * kBatchBY, 2)
+template <class SP, bool IS_PHI, int BX, int ROWS>
+__global__ void __launch_bounds__(BX, 1024 / BX)
 k_batch_step(const BatchInst* __restrict__ inst, const int* __restrict__ tile_inst, int ntiles,
              const typename SP::store_t* __restrict__ fin, typename SP::store_t* __restrict__ fout,
              const typename SP::real* __restrict__ phi_n, const typename SP::real* __restrict__ phi_np1,
              const typename SP::real* __restrict__ c_n, typename SP::real* __restrict__ moment_out) {
+    // the tile's instance parameters live in shared memory while it is marched:
+    // read through a global pointer they would be reloaded (they may alias the
+    // stores) on every use inside the link loops
+    __shared__ KParams sK;
+    static_assert(sizeof(KParams) % 4 == 0, "copied as 32-bit words");
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         __syncthreads();   // the previous tile's shared memory is free
         const BatchInst& I = inst[tile_inst[t]];
+        const int* src = reinterpret_cast<const int*>(&I.Km);
+        int* dst = reinterpret_cast<int*>(&sK);
+        for (int w = threadIdx.x; w < (int)(sizeof(KParams) / 4); w += blockDim.x) dst[w] = src[w];
         const int lt = t - I.tile_begin;
-        const int x0 = (lt % I.tiles_x) * 32;
-        const int y0 = (lt / I.tiles_x) * kBatchBY;
+        const int x0 = (lt % I.tiles_x) * BX;
+        const int z0 = (lt / I.tiles_x) * ROWS;
         const long long po = I.pop_off, fo = I.fld_off;
+        const bool walls = I.walls != 0;
+        __syncthreads();
         const typename SP::real* pn1 = phi_np1 ? phi_np1 + fo : nullptr;
-        if (I.walls)
-            march<D2Q9, SP, kBatchBY, 1, IS_PHI, true>(I.K, fin + po, fout + po, phi_n + fo, pn1, c_n + fo,
-                                                       moment_out + fo, nullptr, x0, y0, 0, 0);
+        if (walls)
+            march<D2Q9R, SP, 1, ROWS, IS_PHI, true, BX>(sK, fin + po, fout + po, phi_n + fo, pn1, c_n + fo,
+                                                        moment_out + fo, nullptr, x0, 0, z0, 0);
         else
-            march<D2Q9, SP, kBatchBY, 1, IS_PHI, false>(I.K, fin + po, fout + po, phi_n + fo, pn1, c_n + fo,
-                                                        moment_out + fo, nullptr, x0, y0, 0, 0);
+            march<D2Q9R, SP, 1, ROWS, IS_PHI, false, BX>(sK, fin + po, fout + po, phi_n + fo, pn1, c_n + fo,
+                                                         moment_out + fo, nullptr, x0, 0, z0, 0);
     }
 }
 
-template <class SP>
+template <class SP, int BX, int ROWS>
 constexpr size_t batch_smem(bool is_phi) {
-    return march_smem<D2Q9, SP, kBatchBY, 1>(is_phi);
+    return march_smem<D2Q9R, SP, 1, ROWS, BX>(is_phi);
 }
 
 }  // namespace lbpf

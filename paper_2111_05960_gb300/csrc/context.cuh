@@ -31,9 +31,10 @@ struct Dispatch {
                        void* c_out, double* mass_partials);
     void (*launch_corr_p)(lbpf_ctx*, lbpf::MassCorr* mc, void* c, void* h);
 };
-// Launchers of a batch of 2-D instances.
+// Launchers of a batch of 2-D instances; the step kernels use the tile shape
+// ctx->btile (an index into lbpf::kBatchTiles), which prepare() sets up.
 struct BatchDispatch {
-    lbpf_status (*prepare)(lbpf_ctx*);
+    lbpf_status (*prepare)(lbpf_ctx*, int tile);
     void (*launch_phi)(lbpf_ctx*, int cur);
     void (*launch_c)(lbpf_ctx*, int cur);
     void (*launch_init)(lbpf_ctx*, int i);
@@ -58,6 +59,7 @@ struct lbpf_ctx {
     lbpf_params p;
     lbpf::StepParams sp;
     lbpf::KParams kp;
+    lbpf::KParams kpm;             // the marching kernels' view (2-D: rows as z-planes)
     int q = 0;
     size_t real_size = 0, store_size = 0;
     cudaStream_t stream = nullptr;
@@ -87,6 +89,9 @@ struct lbpf_ctx {
     int* d_tile_inst = nullptr;
     int ntiles = 0;
     int persist_blocks = 0;
+    int btile = 0;                        // tile shape in use (index into lbpf::kBatchTiles)
+    double btile_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // autotuner: ms per step of each shape
+    int tile_capacity = 0;                // entries of d_tile_inst
     const lbpf_rt::BatchDispatch* bops = nullptr;
     // two steps captured as a CUDA graph (replayed by lbpf_step)
     cudaGraphExec_t graph = nullptr;
@@ -110,6 +115,21 @@ lbpf_status cuda_fail(lbpf_ctx* ctx, cudaError_t e, const char* what);
 lbpf_status alloc(lbpf_ctx* ctx, void** ptr, size_t bytes, const char* what);
 lbpf_status check_launch(lbpf_ctx* ctx, const char* what);
 lbpf_status ensure_staging(lbpf_ctx* ctx);
+
+lbpf_status validate(const lbpf_params* p, std::string& why);
+lbpf::StepParams lattice_units(const lbpf_params* p);
+lbpf::KParams make_kparams(const lbpf_params* p);
+lbpf::KParams march_kparams(const lbpf::KParams& kp, int lattice);
+void free_all(lbpf_ctx* ctx);
+void set_thread_error(const std::string& msg);
+
+inline bool is_f64(const lbpf_ctx* ctx) { return ctx->p.precision == LBPF_FP64; }
+
+// FP64 caller data -> the compute type, n values
+template <typename R>
+void launch_from_f64(const double* src, void* dst, long long n, cudaStream_t s) {
+    lbpf::k_from_f64<R><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, (R*)dst, n);
+}
 
 // adjoint.cu
 const AdjDispatch* pick_adjoint(int lattice, int precision);

@@ -20,6 +20,7 @@ namespace lbpf {
 struct D2Q9 {
     static constexpr int D = 2;
     static constexpr int Q = 9;
+    static constexpr bool FLAT_Y = false;   // has links along y
     __host__ __device__ static constexpr int ex(int k) {
         return (k == 1 || k == 5 || k == 8) ? 1 : ((k == 3 || k == 6 || k == 7) ? -1 : 0);
     }
@@ -40,6 +41,7 @@ struct D2Q9 {
 struct D3Q19 {
     static constexpr int D = 3;
     static constexpr int Q = 19;
+    static constexpr bool FLAT_Y = false;
     // k: 1..6 faces +x -x +y -y +z -z; 7..18 edges
     // (1,1,0) (-1,-1,0) (1,-1,0) (-1,1,0) (1,0,1) (-1,0,-1) (1,0,-1) (-1,0,1)
     // (0,1,1) (0,-1,-1) (0,1,-1) (0,-1,1)
@@ -63,6 +65,22 @@ struct D3Q19 {
     }
     // w_k = m_k / 36 with integer m_k; the moving links have power-of-two m_k
     __host__ __device__ static constexpr int m(int k) { return k == 0 ? 12 : (k <= 6 ? 2 : 1); }
+};
+
+// D2Q9 with its y links relabelled as z links: the 2-D grid [y][x] read as
+// the 3-D grid [z = y][1][x], so that the z-marching kernels walk the rows of a
+// 2-D domain, each "plane" being a segment of one row.  Same links, weights
+// and ordering as D2Q9; only the kernels' view of the axes changes.
+struct D2Q9R {
+    static constexpr int D = 3;               // marched like a 3-D lattice
+    static constexpr int Q = 9;
+    static constexpr bool FLAT_Y = true;      // no links along the (unit) y axis
+    __host__ __device__ static constexpr int ex(int k) { return D2Q9::ex(k); }
+    __host__ __device__ static constexpr int ey(int) { return 0; }
+    __host__ __device__ static constexpr int ez(int k) { return D2Q9::ey(k); }
+    __host__ __device__ static constexpr double w(int k) { return D2Q9::w(k); }
+    __host__ __device__ static constexpr int opp(int k) { return D2Q9::opp(k); }
+    __host__ __device__ static constexpr int m(int k) { return D2Q9::m(k); }
 };
 
 }  // namespace lbpf

@@ -23,6 +23,7 @@ thread_local std::string g_thread_error;
 }  // namespace
 
 void lbpf_internal_set_thread_error(const std::string& msg) { g_thread_error = msg; }
+void lbpf_rt::set_thread_error(const std::string& msg) { g_thread_error = msg; }
 
 // ---- helpers shared with adjoint.cu ---------------------------------------------
 
@@ -64,13 +65,18 @@ namespace {
 
 // ---- per (lattice, storage) dispatch ---------------------------------------------
 
-// Tile shapes: 32 x BY threads per block, ZCH planes per block in 3-D, at least
-// MINB resident blocks per SM (register budget).  Overridable at build time.
-#ifndef LBPF_BY2
-#define LBPF_BY2 8
+// Tile shapes of the z-marching kernels: BX x BY threads per block, ZCH planes
+// per block, at least MINB resident blocks per SM (register budget).  2-D
+// domains march along y through the D2Q9R view: BX-long row segments, ZCH rows
+// per block.  Overridable at build time.
+#ifndef LBPF_BX2
+#define LBPF_BX2 128
+#endif
+#ifndef LBPF_YCH2
+#define LBPF_YCH2 16
 #endif
 #ifndef LBPF_MINB2
-#define LBPF_MINB2 2
+#define LBPF_MINB2 6
 #endif
 #ifndef LBPF_BY3
 #define LBPF_BY3 8
@@ -91,9 +97,15 @@ constexpr double kCorrDelta = 1e-5;
 template <class L>
 struct TileCfg;
 template <>
-struct TileCfg<D2Q9> { static constexpr int BY = LBPF_BY2, ZCH = 1, MINB = LBPF_MINB2; };
+struct TileCfg<D2Q9> {
+    using ML = D2Q9R;
+    static constexpr int BX = LBPF_BX2, BY = 1, ZCH = LBPF_YCH2, MINB = LBPF_MINB2;
+};
 template <>
-struct TileCfg<D3Q19> { static constexpr int BY = LBPF_BY3, ZCH = LBPF_ZCH3, MINB = LBPF_MINB3; };
+struct TileCfg<D3Q19> {
+    using ML = D3Q19;
+    static constexpr int BX = 32, BY = LBPF_BY3, ZCH = LBPF_ZCH3, MINB = LBPF_MINB3;
+};
 template <class L, class SP>
 constexpr int min_blocks() {
     return (L::D == 3 && sizeof(typename SP::real) == 8) ? LBPF_MINB3_F64 : TileCfg<L>::MINB;
@@ -103,40 +115,42 @@ template <class L, class SP>
 struct Impl {
     using R = typename SP::real;
     using S = typename SP::store_t;
-    static constexpr int BY = TileCfg<L>::BY, ZCH = TileCfg<L>::ZCH, MINB = min_blocks<L, SP>();
-    static constexpr size_t smem_phi = march_smem<L, SP, BY, ZCH>(true);
-    static constexpr size_t smem_c = march_smem<L, SP, BY, ZCH>(false);
+    using ML = typename TileCfg<L>::ML;     // the lattice as the marching kernels see it
+    static constexpr int BX = TileCfg<L>::BX, BY = TileCfg<L>::BY, ZCH = TileCfg<L>::ZCH,
+                         MINB = min_blocks<L, SP>();
+    static constexpr size_t smem_phi = march_smem<ML, SP, BY, ZCH, BX>(true);
+    static constexpr size_t smem_c = march_smem<ML, SP, BY, ZCH, BX>(false);
+    template <bool W>
+    static constexpr auto kphi() { return k_phi_step<ML, SP, BY, ZCH, MINB, W, BX>; }
+    template <bool W>
+    static constexpr auto kc() { return k_c_step<ML, SP, BY, ZCH, MINB, W, BX>; }
 
     static lbpf_status prepare(lbpf_ctx* ctx) {
-        LBPF_CUDA(ctx, cudaFuncSetAttribute(k_phi_step<L, SP, BY, ZCH, MINB, true>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_phi));
-        LBPF_CUDA(ctx, cudaFuncSetAttribute(k_c_step<L, SP, BY, ZCH, MINB, true>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
-        LBPF_CUDA(ctx, cudaFuncSetAttribute(k_phi_step<L, SP, BY, ZCH, MINB, false>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_phi));
-        LBPF_CUDA(ctx, cudaFuncSetAttribute(k_c_step<L, SP, BY, ZCH, MINB, false>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
+        LBPF_CUDA(ctx, cudaFuncSetAttribute(kphi<true>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_phi));
+        LBPF_CUDA(ctx, cudaFuncSetAttribute(kc<true>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
+        LBPF_CUDA(ctx, cudaFuncSetAttribute(kphi<false>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_phi));
+        LBPF_CUDA(ctx, cudaFuncSetAttribute(kc<false>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
         return LBPF_OK;
     }
     static bool walls(const lbpf_ctx* ctx) {
         const StepParams& P = ctx->sp;
         return P.bc[0] || P.bc[1] || (L::D == 3 && P.bc[2]);
     }
+    // grid over the marching view (kpm: 2-D domains as [ny][1][nx])
     static dim3 grid(const lbpf_ctx* ctx) {
-        const StepParams& P = ctx->sp;
-        const int zblocks = L::D == 3 ? (P.nz + ZCH - 1) / ZCH : 1;
-        return dim3((P.nx + 31) / 32, (P.ny + BY - 1) / BY, zblocks);
+        const StepParams& P = ctx->kpm.P;
+        return dim3((P.nx + BX - 1) / BX, (P.ny + BY - 1) / BY, (P.nz + ZCH - 1) / ZCH);
     }
     static void launch_phi_p(lbpf_ctx* ctx, const void* g, void* g_out, const void* phi, const void* c,
                              void* phi_out) {
-        auto kern = walls(ctx) ? k_phi_step<L, SP, BY, ZCH, MINB, true> : k_phi_step<L, SP, BY, ZCH, MINB, false>;
-        kern<<<grid(ctx), dim3(32, BY), smem_phi, ctx->stream>>>(ctx->kp, (const S*)g, (S*)g_out, (const R*)phi,
+        auto kern = walls(ctx) ? kphi<true>() : kphi<false>();
+        kern<<<grid(ctx), dim3(BX, BY), smem_phi, ctx->stream>>>(ctx->kpm, (const S*)g, (S*)g_out, (const R*)phi,
                                                                    (const R*)c, (R*)phi_out);
     }
     static void launch_c_p(lbpf_ctx* ctx, const void* h, void* h_out, const void* phi, const void* phi_out,
                            const void* c, void* c_out, double* mass_partials) {
-        auto kern = walls(ctx) ? k_c_step<L, SP, BY, ZCH, MINB, true> : k_c_step<L, SP, BY, ZCH, MINB, false>;
-        kern<<<grid(ctx), dim3(32, BY), smem_c, ctx->stream>>>(ctx->kp, (const S*)h, (S*)h_out, (const R*)phi,
+        auto kern = walls(ctx) ? kc<true>() : kc<false>();
+        kern<<<grid(ctx), dim3(BX, BY), smem_c, ctx->stream>>>(ctx->kpm, (const S*)h, (S*)h_out, (const R*)phi,
                                                                  (const R*)phi_out, (const R*)c, (R*)c_out,
                                                                  mass_partials);
     }
@@ -208,82 +222,11 @@ const Dispatch* pick(int lattice, int precision) {
     return nullptr;
 }
 
-// ---- batch of 2-D instances -------------------------------------------------------
+}  // namespace
 
+// ---- helpers shared with batch.cu and adjoint.cu -----------------------------------
 
-template <class SP>
-struct BatchImpl {
-    using R = typename SP::real;
-    using S = typename SP::store_t;
-    static constexpr size_t smem_phi = batch_smem<SP>(true);
-    static constexpr size_t smem_c = batch_smem<SP>(false);
-
-    static lbpf_status prepare(lbpf_ctx* ctx) {
-        LBPF_CUDA(ctx, cudaFuncSetAttribute(k_batch_step<SP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)smem_phi));
-        LBPF_CUDA(ctx, cudaFuncSetAttribute(k_batch_step<SP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)smem_c));
-        int sms = 0, occ_phi = 0, occ_c = 0;
-        LBPF_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
-        LBPF_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_phi, k_batch_step<SP, true>,
-                                                                     32 * kBatchBY, smem_phi));
-        LBPF_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_c, k_batch_step<SP, false>,
-                                                                     32 * kBatchBY, smem_c));
-        const int occ = std::max(1, std::min(occ_phi, occ_c));
-        ctx->persist_blocks = std::max(1, std::min(ctx->ntiles, sms * occ));
-        return LBPF_OK;
-    }
-    static void launch_phi(lbpf_ctx* ctx, int cur) {
-        const int nxt = cur ^ 1;
-        k_batch_step<SP, true><<<ctx->persist_blocks, dim3(32, kBatchBY), smem_phi, ctx->stream>>>(
-            ctx->d_binst, ctx->d_tile_inst, ctx->ntiles, (const S*)ctx->g[cur], (S*)ctx->g[nxt],
-            (const R*)ctx->phi[cur], nullptr, (const R*)ctx->c[cur], (R*)ctx->phi[nxt]);
-    }
-    static void launch_c(lbpf_ctx* ctx, int cur) {
-        const int nxt = cur ^ 1;
-        k_batch_step<SP, false><<<ctx->persist_blocks, dim3(32, kBatchBY), smem_c, ctx->stream>>>(
-            ctx->d_binst, ctx->d_tile_inst, ctx->ntiles, (const S*)ctx->h[cur], (S*)ctx->h[nxt],
-            (const R*)ctx->phi[cur], (const R*)ctx->phi[nxt], (const R*)ctx->c[cur], (R*)ctx->c[nxt]);
-    }
-    static void launch_init(lbpf_ctx* ctx, int i) {
-        const BatchInst& I = ctx->binst[i];
-        const int cur = ctx->cur;
-        k_init<D2Q9, SP><<<(unsigned)((I.K.P.N + 255) / 256), 256, 0, ctx->stream>>>(
-            I.K, (const R*)ctx->phi[cur] + I.fld_off, (R*)ctx->c[cur] + I.fld_off, (S*)ctx->g[cur] + I.pop_off,
-            (S*)ctx->h[cur] + I.pop_off);
-    }
-    static void fields_out(lbpf_ctx* ctx, int i, double* ophi, double* oc, double* omu) {
-        const BatchInst& I = ctx->binst[i];
-        const int cur = ctx->cur;
-        k_fields_out<R><<<(unsigned)((I.K.P.N + 255) / 256), 256, 0, ctx->stream>>>(
-            I.K, (const R*)ctx->phi[cur] + I.fld_off, (const R*)ctx->c[cur] + I.fld_off, ophi, oc, omu);
-    }
-    static void pop_mass(lbpf_ctx* ctx, int i) {
-        const BatchInst& I = ctx->binst[i];
-        const int cur = ctx->cur;
-        const int blocks = (int)std::min<long long>((I.K.P.N + kMassThreads - 1) / kMassThreads, ctx->mass_blocks);
-        k_pop_mass<D2Q9, SP><<<blocks, kMassThreads, 0, ctx->stream>>>(
-            I.K, (const R*)ctx->phi[cur] + I.fld_off, (const R*)ctx->c[cur] + I.fld_off,
-            (const S*)ctx->h[cur] + I.pop_off, ctx->partials);
-        k_mass_final<<<1, kMassThreads, 0, ctx->stream>>>(ctx->partials, blocks, ctx->mass_out);
-    }
-    static const BatchDispatch* table() {
-        static const BatchDispatch d = {prepare, launch_phi, launch_c, launch_init, fields_out, pop_mass};
-        return &d;
-    }
-};
-
-const BatchDispatch* pick_batch(int precision) {
-    switch (precision) {
-        case LBPF_FP64: return BatchImpl<StoreF64>::table();
-        case LBPF_FP32: return BatchImpl<StoreF32>::table();
-        case LBPF_FP32_BF16DEV: return BatchImpl<StoreBF16Dev>::table();
-        case LBPF_FP32_FP16DEV: return BatchImpl<StoreF16Dev>::table();
-    }
-    return nullptr;
-}
-
-lbpf_status validate(const lbpf_params* p, std::string& why) {
+lbpf_status lbpf_rt::validate(const lbpf_params* p, std::string& why) {
     auto bad = [&](const char* m) { why = m; return LBPF_EINVAL; };
     if (p->nx < 1 || p->ny < 1 || p->nz < 1) return bad("grid sizes must be >= 1");
     if (p->lattice != LBPF_D2Q9 && p->lattice != LBPF_D3Q19) return bad("unknown lattice");
@@ -310,7 +253,7 @@ lbpf_status validate(const lbpf_params* p, std::string& why) {
     return LBPF_OK;
 }
 
-StepParams lattice_units(const lbpf_params* p) {
+StepParams lbpf_rt::lattice_units(const lbpf_params* p) {
     StepParams s;
     s.nx = p->nx; s.ny = p->ny; s.nz = p->nz;
     for (int a = 0; a < 3; ++a) s.bc[a] = p->bc[a];
@@ -335,7 +278,7 @@ StepParams lattice_units(const lbpf_params* p) {
 }
 
 // Geometry, coefficients (FP64 and FP32) and link offsets of one simulation.
-KParams make_kparams(const lbpf_params* p) {
+KParams lbpf_rt::make_kparams(const lbpf_params* p) {
     KParams kp;
     kp.P = lattice_units(p);
     kp.cd = make_coef<double>(kp.P);
@@ -354,7 +297,20 @@ KParams make_kparams(const lbpf_params* p) {
     return kp;
 }
 
-void free_all(lbpf_ctx* ctx) {
+// The marching kernels' view of the grid: a 2-D domain [ny][nx] is walked row by
+// row as the 3-D grid [nz = ny][1][nx] (lattice D2Q9R, same link offsets).
+KParams lbpf_rt::march_kparams(const KParams& kp, int lattice) {
+    KParams m = kp;
+    if (lattice == LBPF_D2Q9) {
+        m.P.nz = kp.P.ny;
+        m.P.ny = 1;
+        m.P.bc[2] = kp.P.bc[1];
+        m.P.bc[1] = LBPF_PERIODIC;
+    }
+    return m;
+}
+
+void lbpf_rt::free_all(lbpf_ctx* ctx) {
     for (int i = 0; i < 2; ++i) {
         cudaFree(ctx->g[i]); cudaFree(ctx->h[i]); cudaFree(ctx->phi[i]); cudaFree(ctx->c[i]);
         ctx->g[i] = ctx->h[i] = ctx->phi[i] = ctx->c[i] = nullptr;
@@ -371,6 +327,8 @@ void free_all(lbpf_ctx* ctx) {
     ctx->graph = nullptr;
     free_adjoint(ctx);
 }
+
+namespace {
 
 // One coupled step (both kernels), followed by the mass correction when it is due.
 void launch_one_step(lbpf_ctx* ctx) {
@@ -451,11 +409,6 @@ long long corr_stride_for(long long N) {
 }
 
 template <typename R>
-void launch_from_f64(const double* src, void* dst, long long n, cudaStream_t s) {
-    k_from_f64<R><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, (R*)dst, n);
-}
-
-template <typename R>
 void launch_fields_out(lbpf_ctx* ctx, double* ophi, double* oc, double* omu) {
     const long long N = ctx->sp.N;
     k_fields_out<R><<<(unsigned)((N + 255) / 256), 256, 0, ctx->stream>>>(
@@ -469,7 +422,6 @@ void launch_mass(lbpf_ctx* ctx) {
     k_mass_final<<<1, kMassThreads, 0, ctx->stream>>>(ctx->partials, ctx->mass_blocks, ctx->mass_out);
 }
 
-bool is_f64(const lbpf_ctx* ctx) { return ctx->p.precision == LBPF_FP64; }
 
 }  // namespace
 
@@ -515,6 +467,7 @@ lbpf_status lbpf_create(const lbpf_params* p, const double* phi0, const double* 
     ctx->sp = lattice_units(p);
     ctx->q = p->lattice == LBPF_D3Q19 ? 19 : 9;
     ctx->kp = make_kparams(p);
+    ctx->kpm = march_kparams(ctx->kp, p->lattice);
     ctx->ops = ops;
     ctx->aops = aops;
     ctx->stream = (cudaStream_t)cuda_stream;
@@ -738,164 +691,6 @@ lbpf_status lbpf_get_populations(lbpf_ctx* ctx, double* g, double* h, int32_t pt
     if (tmp) cudaFree(tmp);
     if (st == LBPF_OK && e != cudaSuccess) st = cuda_fail(ctx, e, "population export");
     return st;
-}
-
-lbpf_status lbpf_create_batch(const lbpf_params* p, int32_t n, const double* const* phi0,
-                              const double* const* c0, int32_t ptr_is_device, void* cuda_stream, lbpf_ctx** out) {
-    if (!out) return fail(nullptr, LBPF_EINVAL, "out pointer is NULL");
-    *out = nullptr;
-    if (!p || !phi0 || !c0 || n < 1) return fail(nullptr, LBPF_EINVAL, "NULL argument or n < 1");
-    for (int i = 0; i < n; ++i) {
-        std::string why;
-        if (!phi0[i] || !c0[i]) return fail(nullptr, LBPF_EINVAL, "NULL field pointer of instance " + std::to_string(i));
-        if (validate(&p[i], why) != LBPF_OK) return fail(nullptr, LBPF_EINVAL, "instance " + std::to_string(i) + ": " + why);
-        if (p[i].lattice != LBPF_D2Q9) return fail(nullptr, LBPF_EUNSUPPORTED, "batches hold 2-D D2Q9 instances");
-        if (p[i].precision != p[0].precision) return fail(nullptr, LBPF_EINVAL, "all instances need one precision");
-        if (p[i].mass_every != 0) return fail(nullptr, LBPF_EUNSUPPORTED, "mass correction is not built for batches");
-        if (p[i].checkpoint_every != 0) return fail(nullptr, LBPF_EUNSUPPORTED, "the adjoint is not built for batches");
-    }
-    const BatchDispatch* bops = pick_batch(p[0].precision);
-    if (!bops) return fail(nullptr, LBPF_EUNSUPPORTED, "precision not built");
-    lbpf_ctx* ctx = new (std::nothrow) lbpf_ctx();
-    if (!ctx) return fail(nullptr, LBPF_ENOMEM, "host allocation failed");
-    ctx->is_batch = true;
-    ctx->nb = n;
-    ctx->bops = bops;
-    ctx->p = p[0];
-    ctx->q = 9;
-    ctx->stream = (cudaStream_t)cuda_stream;
-    ctx->real_size = p[0].precision == LBPF_FP64 ? 8 : 4;
-    ctx->store_size = p[0].precision == LBPF_FP64 ? 8 : (p[0].precision == LBPF_FP32 ? 4 : 2);
-    auto abort_create = [&](lbpf_status st) {
-        std::string m = ctx->err;
-        free_all(ctx);
-        delete ctx;
-        g_thread_error = m;
-        return st;
-    };
-    // instance table: offsets into the concatenated buffers and the flat tile list
-    long long nodes = 0;
-    int tiles = 0;
-    std::vector<int> tile_inst;
-    try {
-        ctx->binst.resize(n);
-        for (int i = 0; i < n; ++i) {
-            BatchInst& I = ctx->binst[i];
-            I.K = make_kparams(&p[i]);
-            I.fld_off = nodes;
-            I.pop_off = 9 * nodes;
-            I.tiles_x = (p[i].nx + 31) / 32;
-            const int ty = (p[i].ny + kBatchBY - 1) / kBatchBY;
-            I.tile_begin = tiles;
-            I.walls = (p[i].bc[0] || p[i].bc[1]) ? 1 : 0;
-            I.pad = 0;
-            for (int t = 0; t < I.tiles_x * ty; ++t) tile_inst.push_back(i);
-            tiles += I.tiles_x * ty;
-            nodes += I.K.P.N;
-        }
-    } catch (...) {
-        return abort_create(fail(ctx, LBPF_ENOMEM, "host allocation failed"));
-    }
-    ctx->ntiles = tiles;
-    // the whole batch as one field of `nodes` values, for lbpf_mass
-    ctx->sp = ctx->binst[0].K.P;
-    ctx->sp.N = nodes;
-    ctx->sp.nx = (int)std::min<long long>(nodes, 1LL << 30);
-    ctx->kp = ctx->binst[0].K;
-    lbpf_status st;
-    cudaError_t e = cudaGetDevice(&ctx->device);
-    if (e != cudaSuccess) { cuda_fail(ctx, e, "cudaGetDevice"); return abort_create(LBPF_ECUDA); }
-    const size_t N = (size_t)nodes;
-    for (int i = 0; i < 2; ++i) {
-        if ((st = alloc(ctx, &ctx->g[i], ctx->store_size * 9 * N, "g populations")) != LBPF_OK) return abort_create(st);
-        if ((st = alloc(ctx, &ctx->h[i], ctx->store_size * 9 * N, "h populations")) != LBPF_OK) return abort_create(st);
-        if ((st = alloc(ctx, &ctx->phi[i], ctx->real_size * N, "phi field")) != LBPF_OK) return abort_create(st);
-        if ((st = alloc(ctx, &ctx->c[i], ctx->real_size * N, "c field")) != LBPF_OK) return abort_create(st);
-    }
-    if ((st = alloc(ctx, (void**)&ctx->d_binst, sizeof(BatchInst) * n, "instance table")) != LBPF_OK) return abort_create(st);
-    if ((st = alloc(ctx, (void**)&ctx->d_tile_inst, sizeof(int) * tiles, "tile list")) != LBPF_OK) return abort_create(st);
-    int sms = 152;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
-    ctx->mass_blocks = (int)std::max<long long>(1, std::min<long long>((nodes + kMassThreads - 1) / kMassThreads, 4LL * sms));
-    if ((st = alloc(ctx, (void**)&ctx->partials, sizeof(double) * 3 * ctx->mass_blocks, "mass partials")) != LBPF_OK) return abort_create(st);
-    if ((st = alloc(ctx, (void**)&ctx->mass_out, sizeof(double) * 3, "mass result")) != LBPF_OK) return abort_create(st);
-    e = cudaMemcpyAsync(ctx->d_binst, ctx->binst.data(), sizeof(BatchInst) * n, cudaMemcpyHostToDevice, ctx->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(ctx->d_tile_inst, tile_inst.data(), sizeof(int) * tiles, cudaMemcpyHostToDevice, ctx->stream);
-    if (e != cudaSuccess) { cuda_fail(ctx, e, "instance table"); return abort_create(LBPF_ECUDA); }
-    if ((st = bops->prepare(ctx)) != LBPF_OK) return abort_create(st);
-    // fields: per instance into the staging buffer (host) or straight from the caller (device)
-    if (!ptr_is_device) {
-        if ((st = ensure_staging(ctx)) != LBPF_OK) return abort_create(st);
-    }
-    for (int i = 0; i < n; ++i) {
-        const BatchInst& I = ctx->binst[i];
-        const size_t Ni = (size_t)I.K.P.N;
-        const double* sphi = phi0[i];
-        const double* sc = c0[i];
-        if (!ptr_is_device) {
-            e = cudaMemcpyAsync(ctx->staging + I.fld_off, phi0[i], sizeof(double) * Ni, cudaMemcpyHostToDevice, ctx->stream);
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync(ctx->staging + N + I.fld_off, c0[i], sizeof(double) * Ni, cudaMemcpyHostToDevice, ctx->stream);
-            if (e != cudaSuccess) { cuda_fail(ctx, e, "copy of phi0/c0"); return abort_create(LBPF_ECUDA); }
-            sphi = ctx->staging + I.fld_off;
-            sc = ctx->staging + N + I.fld_off;
-        }
-        if (is_f64(ctx)) {
-            launch_from_f64<double>(sphi, (double*)ctx->phi[0] + I.fld_off, (long long)Ni, ctx->stream);
-            launch_from_f64<double>(sc, (double*)ctx->c[0] + I.fld_off, (long long)Ni, ctx->stream);
-        } else {
-            launch_from_f64<float>(sphi, (float*)ctx->phi[0] + I.fld_off, (long long)Ni, ctx->stream);
-            launch_from_f64<float>(sc, (float*)ctx->c[0] + I.fld_off, (long long)Ni, ctx->stream);
-        }
-    }
-    ctx->cur = 0;
-    for (int i = 0; i < n; ++i) bops->launch_init(ctx, i);
-    if ((st = check_launch(ctx, "initialisation kernels")) != LBPF_OK) return abort_create(st);
-    e = cudaStreamSynchronize(ctx->stream);
-    if (e != cudaSuccess) { cuda_fail(ctx, e, "initialisation"); return abort_create(LBPF_ECUDA); }
-    *out = ctx;
-    return LBPF_OK;
-}
-
-lbpf_status lbpf_batch_get_fields(lbpf_ctx* ctx, int32_t i, double* phi, double* c, double* mu, int32_t ptr_is_device) {
-    if (!ctx) return fail(nullptr, LBPF_EINVAL, "ctx is NULL");
-    if (!ctx->is_batch) return fail(ctx, LBPF_EINVAL, "not a batch context");
-    if (ctx->poisoned) return fail(ctx, LBPF_ESTATE, "context poisoned by an earlier error");
-    if (i < 0 || i >= ctx->nb) return fail(ctx, LBPF_EINVAL, "instance index out of range");
-    const size_t Ni = (size_t)ctx->binst[i].K.P.N;
-    double *dphi = phi, *dc = c, *dmu = mu;
-    if (!ptr_is_device) {
-        lbpf_status st = ensure_staging(ctx);
-        if (st != LBPF_OK) return st;
-        dphi = phi ? ctx->staging : nullptr;
-        dc = c ? ctx->staging + Ni : nullptr;
-        dmu = mu ? ctx->staging + 2 * Ni : nullptr;
-    }
-    ctx->bops->fields_out(ctx, i, dphi, dc, dmu);
-    lbpf_status st = check_launch(ctx, "field export kernel");
-    if (st != LBPF_OK) return st;
-    if (!ptr_is_device) {
-        if (phi) LBPF_CUDA(ctx, cudaMemcpyAsync(phi, dphi, sizeof(double) * Ni, cudaMemcpyDeviceToHost, ctx->stream));
-        if (c) LBPF_CUDA(ctx, cudaMemcpyAsync(c, dc, sizeof(double) * Ni, cudaMemcpyDeviceToHost, ctx->stream));
-        if (mu) LBPF_CUDA(ctx, cudaMemcpyAsync(mu, dmu, sizeof(double) * Ni, cudaMemcpyDeviceToHost, ctx->stream));
-    }
-    LBPF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    return LBPF_OK;
-}
-
-lbpf_status lbpf_batch_solute_mass(lbpf_ctx* ctx, double* masses) {
-    if (!ctx || !masses) return fail(ctx, LBPF_EINVAL, "NULL argument");
-    if (!ctx->is_batch) return fail(ctx, LBPF_EINVAL, "not a batch context");
-    if (ctx->poisoned) return fail(ctx, LBPF_ESTATE, "context poisoned by an earlier error");
-    for (int i = 0; i < ctx->nb; ++i) {
-        ctx->bops->pop_mass(ctx, i);
-        lbpf_status st = check_launch(ctx, "population mass kernels");
-        if (st != LBPF_OK) return st;
-        LBPF_CUDA(ctx, cudaMemcpyAsync(&masses[i], ctx->mass_out, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-    }
-    LBPF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    return LBPF_OK;
 }
 
 lbpf_status lbpf_get_step(const lbpf_ctx* ctx, int64_t* step) {

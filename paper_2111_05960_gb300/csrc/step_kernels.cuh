@@ -209,8 +209,9 @@ __device__ __forceinline__ R p_term(const Coef<R>& C, R phi, R mu) {
 }
 
 // ---- z-marching tile geometry ------------------------------------------------------
-// A block of 32 x BY threads owns an x-y tile and walks a chunk of ZCH planes
-// along z (2-D: one plane).  Shared memory holds rolling windows: phi^n for the
+// A block of BX x BY threads owns an x-y tile and walks a chunk of ZCH planes
+// along z.  2-D domains are walked row by row through the D2Q9R view (planes
+// are BX-long row segments, BY = 1, no y ring).  Shared memory holds rolling windows: phi^n for the
 // planes z-2..z+2 with a 2-node x-y halo, and the per-node ingredients for the
 // planes z-1..z+1 with a 1-node x-y ring.
 
@@ -219,11 +220,13 @@ struct alignas(4 * sizeof(R)) V4 {
     R a, b, c, d;
 };
 
-template <class L, int BY>
+template <class L, int BY, int BX_>
 struct Geo {
-    static constexpr int BX = 32;
-    static constexpr int X2 = BX + 4, Y2 = BY + 4;   // phi plane with a 2-node halo
-    static constexpr int X1 = BX + 2, Y1 = BY + 2;   // ingredient plane with a 1-node ring
+    static constexpr int BX = BX_;
+    static constexpr int HY = L::FLAT_Y ? 0 : 1;      // y halo needed (links along y)
+    static constexpr int OY1 = HY, OY2 = 2 * HY;      // first tile row in the 1- and 2-halo planes
+    static constexpr int X2 = BX + 4, Y2 = BY + 2 * OY2;   // phi plane with a 2-node halo
+    static constexpr int X1 = BX + 2, Y1 = BY + 2 * OY1;   // ingredient plane with a 1-node ring
     static constexpr int P2 = X2 * Y2, P1 = X1 * Y1;
     static constexpr int NPHI = (L::D == 3) ? 5 : 1; // phi planes in the window
     static constexpr int NING = (L::D == 3) ? 3 : 1; // ingredient planes in the window
@@ -252,10 +255,10 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 // Start the copy of one phi plane (global z index zg, possibly outside) with its
 // 2-node halo (wrapped or mirrored).
-template <class L, int BY, typename R>
+template <class L, int BY, int BX, typename R>
 __device__ __forceinline__ void async_phi_plane(const StepParams& P, const R* __restrict__ phi, R* dst,
                                                 int x0, int y0, int zg, bool inside2) {
-    using G = Geo<L, BY>;
+    using G = Geo<L, BY, BX>;
     const int tid = threadIdx.x + G::BX * threadIdx.y;
     const int gz = (L::D == 3) ? map_coord(zg, P.nz, P.bc[2]) : 0;
     const R* src = phi + (long long)gz * P.nx * P.ny;
@@ -265,7 +268,7 @@ __device__ __forceinline__ void async_phi_plane(const StepParams& P, const R* __
         const int s = tid + it * G::NT;
         if (s < G::P2) {
             const int ly = s / G::X2, lx = s - ly * G::X2;
-            int gx = x0 + lx - 2, gy = y0 + ly - 2;
+            int gx = x0 + lx - 2, gy = y0 + ly - G::OY2;
             if (!inside2) {
                 gx = map_coord(gx, P.nx, P.bc[0]);
                 gy = map_coord(gy, P.ny, P.bc[1]);
@@ -278,10 +281,10 @@ __device__ __forceinline__ void async_phi_plane(const StepParams& P, const R* __
 // grad(phi) by directional derivatives (Eq. DerivDirec_Grad, Eq. Grad) at offset c
 // of the plane p0, with pm / pp the planes below / above.  Opposite links give
 // the same term, so each pair is counted once, doubled.
-template <class L, int BY, typename R>
+template <class L, int BY, int BX, typename R>
 __device__ __forceinline__ void plane_gradient(const R* pm, const R* p0, const R* pp, int c,
                                                R& gx, R& gy, R& gz) {
-    using G = Geo<L, BY>;
+    using G = Geo<L, BY, BX>;
     gx = gy = gz = R(0);
 #pragma unroll
     for (int k = 1; k < L::Q; ++k) {
@@ -303,10 +306,10 @@ __device__ __forceinline__ void plane_gradient(const R* pm, const R* p0, const R
 }
 
 // Linear index of the ring node (lx, ly) of plane zg (1-node ring, maybe outside).
-template <class L, int BY>
+template <class L, int BY, int BX>
 __device__ __forceinline__ long long ring_index(const StepParams& P, int x0, int y0, int lx, int ly, int gz,
                                                 bool inside1) {
-    int gx = x0 + lx - 1, gy = y0 + ly - 1;
+    int gx = x0 + lx - 1, gy = y0 + ly - Geo<L, BY, BX>::OY1;
     if (!inside1) {
         gx = wrap1(gx, P.nx, P.bc[0]);
         gy = wrap1(gy, P.ny, P.bc[1]);
@@ -315,10 +318,10 @@ __device__ __forceinline__ long long ring_index(const StepParams& P, int x0, int
 }
 
 // Start the copy of a field on the 1-node ring of plane zg into shared memory.
-template <class L, int BY, typename R>
+template <class L, int BY, int BX, typename R>
 __device__ __forceinline__ void async_ring(const StepParams& P, const R* __restrict__ f, R* dst, int x0, int y0,
                                            int zg, bool inside1) {
-    using G = Geo<L, BY>;
+    using G = Geo<L, BY, BX>;
     const int tid = threadIdx.x + G::BX * threadIdx.y;
     const int gz = (L::D == 3) ? map_coord(zg, P.nz, P.bc[2]) : 0;
     constexpr int IT = (G::P1 + G::NT - 1) / G::NT;
@@ -327,17 +330,17 @@ __device__ __forceinline__ void async_ring(const StepParams& P, const R* __restr
         const int s = tid + it * G::NT;
         if (s < G::P1) {
             const int ly = s / G::X1, lx = s - ly * G::X1;
-            cp_async(dst + s, f + ring_index<L, BY>(P, x0, y0, lx, ly, gz, inside1));
+            cp_async(dst + s, f + ring_index<L, BY, BX>(P, x0, y0, lx, ly, gz, inside1));
         }
     }
 }
 
 // Ingredients of the phi collision on one plane: alpha_g, beta_g (x, y, z) and
 // A = G^st + G^dw.
-template <class L, int BY, typename R>
+template <class L, int BY, int BX, typename R>
 __device__ __forceinline__ void phi_ingredients(const StepParams& P, const Coef<R>& C, const R* cst,
                                                 const R* pm, const R* p0, const R* pp, V4<R>* ing, R* sA) {
-    using G = Geo<L, BY>;
+    using G = Geo<L, BY, BX>;
     const int tid = threadIdx.x + G::BX * threadIdx.y;
     const R half_src = R(1) - R(0.5) * C.omg;
     constexpr int IT = (G::P1 + G::NT - 1) / G::NT;
@@ -346,7 +349,7 @@ __device__ __forceinline__ void phi_ingredients(const StepParams& P, const Coef<
         const int s = tid + it * G::NT;
         if (s >= G::P1) break;
         const int ly = s / G::X1, lx = s - ly * G::X1;
-        const int c2 = (ly + 1) * G::X2 + (lx + 1);
+        const int c2 = (ly + G::OY2 - G::OY1) * G::X2 + (lx + 1);
         const R ph = p0[c2];
         const R mu = closure_mu(C, ph, cst[s]);
         const R A = g_isotropic(C, ph, mu);
@@ -354,7 +357,7 @@ __device__ __forceinline__ void phi_ingredients(const StepParams& P, const Coef<
         v.a = (C.omg * ph + half_src * A) / R(36);      // per unit m_k (w_k = m_k / 36)
         if (P.counter_term) {
             R gx, gy, gz_;
-            plane_gradient<L, BY>(pm, p0, pp, c2, gx, gy, gz_);
+            plane_gradient<L, BY, BX>(pm, p0, pp, c2, gx, gy, gz_);
             const R inv = rsqrt_reg<R>(gx * gx + gy * gy + gz_ * gz_, C.eps2);
             const R k = C.kct36 * ph * (R(1) - ph) * inv;   // (4/W) phi (1 - phi) n, per unit m_k
             v.b = k * gx; v.c = k * gy; v.d = k * gz_;
@@ -368,10 +371,10 @@ __device__ __forceinline__ void phi_ingredients(const StepParams& P, const Coef<
 
 // Ingredients of the h collision on one plane: P = gamma D mu and
 // beta_h = (1 - w_h/2) gamma (mu D' grad phi + j_at).
-template <class L, int BY, typename R>
+template <class L, int BY, int BX, typename R>
 __device__ __forceinline__ void c_ingredients(const StepParams& P, const Coef<R>& C, const R* cst, const R* pst,
                                               const R* pm, const R* p0, const R* pp, V4<R>* ing) {
-    using G = Geo<L, BY>;
+    using G = Geo<L, BY, BX>;
     const int tid = threadIdx.x + G::BX * threadIdx.y;
     constexpr int IT = (G::P1 + G::NT - 1) / G::NT;
 #pragma unroll
@@ -379,12 +382,12 @@ __device__ __forceinline__ void c_ingredients(const StepParams& P, const Coef<R>
         const int s = tid + it * G::NT;
         if (s >= G::P1) break;
         const int ly = s / G::X1, lx = s - ly * G::X1;
-        const int c2 = (ly + 1) * G::X2 + (lx + 1);
+        const int c2 = (ly + G::OY2 - G::OY1) * G::X2 + (lx + 1);
         const R ph = p0[c2];
         const R dphi = pst[s] - ph;                        // explicit Euler dphi/dt
         const R mu = closure_mu(C, ph, cst[s]);
         R gx, gy, gz_;
-        plane_gradient<L, BY>(pm, p0, pp, c2, gx, gy, gz_);
+        plane_gradient<L, BY, BX>(pm, p0, pp, c2, gx, gy, gz_);
         const R inv = rsqrt_reg<R>(gx * gx + gy * gy + gz_ * gz_, C.eps2);
         const R f = mu * C.Dp + C.atk * dphi * inv;        // F = (mu D' + j_at / |grad|) grad
         V4<R> v;
@@ -480,7 +483,7 @@ __device__ __forceinline__ void pull_load(const KParams& K, const typename SP::s
 // Collision of each pulled population at its upstream node from the ingredient
 // planes im (z-1), i0 (z), ip (z+1) (phi planes fm, f0, fp likewise), the new
 // moment, and the stores.
-template <class L, class SP, int BY, bool IS_PHI, bool WALLS>
+template <class L, class SP, int BY, int BX, bool IS_PHI, bool WALLS>
 __device__ __forceinline__ void pull_combine(const KParams& K, const Coef<typename SP::real>& C,
                                              typename SP::store_t* __restrict__ fout,
                                              const V4<typename SP::real>* im, const V4<typename SP::real>* i0,
@@ -492,11 +495,11 @@ __device__ __forceinline__ void pull_combine(const KParams& K, const Coef<typena
                                              const PullState<L, SP, IS_PHI, WALLS>& st,
                                              MassAcc<typename SP::real>& macc) {
     using R = typename SP::real;
-    using G = Geo<L, BY>;
+    using G = Geo<L, BY, BX>;
     const long long xi = st.xi;
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int c1 = (ty + 1) * G::X1 + (tx + 1);
-    const int c2 = (ty + 2) * G::X2 + (tx + 2);
+    const int c1 = (ty + G::OY1) * G::X1 + (tx + 1);
+    const int c2 = (ty + G::OY2) * G::X2 + (tx + 2);
     const R om = IS_PHI ? C.omg : C.omh;
     const R keep = R(1) - om;
     // without deviation storage a population is stored as soon as it is known
@@ -574,7 +577,7 @@ __device__ __forceinline__ void block_mass_out(const MassAcc<R>& m, double* __re
     __shared__ double red[NT / 32];
     double v = (double)m.hi + (double)m.lo;
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int tid = threadIdx.x + 32 * threadIdx.y;
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
     if ((tid & 31) == 0) red[tid >> 5] = v;
     __syncthreads();
     if (tid == 0) {
@@ -587,7 +590,7 @@ __device__ __forceinline__ void block_mass_out(const MassAcc<R>& m, double* __re
 // One z-marching pass of either kernel.  The composition kernel also sums the
 // exact mass of the populations it writes into mass_partials (one FP64 value
 // per block) when that pointer is not null.
-template <class L, class SP, int BY, int ZCH, bool IS_PHI, bool WALLS>
+template <class L, class SP, int BY, int ZCH, bool IS_PHI, bool WALLS, int BX = 32>
 __device__ __forceinline__ void march(const KParams& K, const typename SP::store_t* __restrict__ fin,
                                       typename SP::store_t* __restrict__ fout,
                                       const typename SP::real* __restrict__ phi_n,
@@ -597,7 +600,7 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
                                       double* __restrict__ mass_partials, int x0, int y0, int z0,
                                       long long mass_slot) {
     using R = typename SP::real;
-    using G = Geo<L, BY>;
+    using G = Geo<L, BY, BX>;
     const StepParams& P = K.P;
     const Coef<R>& C = coef<R>(K);
     extern __shared__ __align__(32) unsigned char smem_raw[];
@@ -609,40 +612,26 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
 
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     const bool active_xy = x < P.nx && y < P.ny;
-    const bool inside2 = x0 >= 2 && x0 + G::BX + 2 <= P.nx && y0 >= 2 && y0 + BY + 2 <= P.ny;
-    const bool inside1 = x0 >= 1 && x0 + G::BX + 1 <= P.nx && y0 >= 1 && y0 + BY + 1 <= P.ny;
+    const bool inside2 = x0 >= 2 && x0 + G::BX + 2 <= P.nx && y0 >= G::OY2 && y0 + BY + G::OY2 <= P.ny;
+    const bool inside1 = x0 >= 1 && x0 + G::BX + 1 <= P.nx && y0 >= G::OY1 && y0 + BY + G::OY1 <= P.ny;
     PullState<L, SP, IS_PHI, WALLS> st;
     MassAcc<R> macc{R(0), R(0)};
 
     // the ring inputs of plane zg go to stage buffer zg & 1
     auto fetch_ring = [&](int zg) {
         const int b = zg & 1;
-        async_ring<L, BY>(P, c_n, cst + b * G::P1, x0, y0, zg, inside1);
-        if (!IS_PHI) async_ring<L, BY>(P, phi_np1, pst + b * G::P1, x0, y0, zg, inside1);
+        async_ring<L, BY, BX>(P, c_n, cst + b * G::P1, x0, y0, zg, inside1);
+        if (!IS_PHI) async_ring<L, BY, BX>(P, phi_np1, pst + b * G::P1, x0, y0, zg, inside1);
     };
     auto ingredients = [&](int slot_i, const R* pm, const R* p0, const R* pp, int zg) {
         const int b = zg & 1;
         if (IS_PHI)
-            phi_ingredients<L, BY>(P, C, cst + b * G::P1, pm, p0, pp, sing + slot_i * G::P1, sA + slot_i * G::P1);
+            phi_ingredients<L, BY, BX>(P, C, cst + b * G::P1, pm, p0, pp, sing + slot_i * G::P1, sA + slot_i * G::P1);
         else
-            c_ingredients<L, BY>(P, C, cst + b * G::P1, pst + b * G::P1, pm, p0, pp, sing + slot_i * G::P1);
+            c_ingredients<L, BY, BX>(P, C, cst + b * G::P1, pst + b * G::P1, pm, p0, pp, sing + slot_i * G::P1);
     };
 
-    if (L::D == 2) {
-        async_phi_plane<L, BY>(P, phi_n, sphi, x0, y0, 0, inside2);
-        fetch_ring(0);
-        cp_async_commit();
-        if (active_xy) pull_load<L, SP, IS_PHI, WALLS>(K, fin, c_n, x, y, 0, inside1, st);
-        cp_async_wait_all();
-        __syncthreads();
-        ingredients(0, sphi, sphi, sphi, 0);
-        __syncthreads();
-        if (active_xy)
-            pull_combine<L, SP, BY, IS_PHI, WALLS>(K, C, fout, sing, sing, sing, sphi, sphi, sphi, sA, phi_np1,
-                                                   moment_out, st, macc);
-        if (!IS_PHI && mass_partials) block_mass_out<G::NT>(macc, mass_partials, mass_slot);
-        return;
-    }
+    static_assert(L::D == 3, "2-D domains march through the D2Q9R view");
 
     // z-march.  While plane z is pulled, the phi plane z+3 and the ring of z+2
     // stream into shared memory, and the loads of plane z overlap the
@@ -651,7 +640,7 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
     auto fslot = [&](int zg) { return sphi + ((zg - z0 + 2 + 5 * ZCH) % 5) * G::P2; };
     auto islot = [&](int zg) { return (zg - z0 + 1 + 3 * ZCH) % 3; };
 
-    for (int zg = z0 - 2; zg <= z0 + 1; ++zg) async_phi_plane<L, BY>(P, phi_n, fslot(zg), x0, y0, zg, inside2);
+    for (int zg = z0 - 2; zg <= z0 + 1; ++zg) async_phi_plane<L, BY, BX>(P, phi_n, fslot(zg), x0, y0, zg, inside2);
     fetch_ring(z0 - 1);
     cp_async_commit();
     cp_async_wait_all();
@@ -663,7 +652,7 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
     cp_async_wait_all();
     __syncthreads();
     ingredients(islot(z0), fslot(z0 - 1), fslot(z0), fslot(z0 + 1), z0);
-    async_phi_plane<L, BY>(P, phi_n, fslot(z0 + 2), x0, y0, z0 + 2, inside2);
+    async_phi_plane<L, BY, BX>(P, phi_n, fslot(z0 + 2), x0, y0, z0 + 2, inside2);
     fetch_ring(z0 + 1);
     cp_async_commit();
     for (int z = z0; z < z1; ++z) {
@@ -671,7 +660,7 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
         __syncthreads();                 // ... for every thread; pull(z-1) is done everywhere
         if (z + 1 < z1) {
             // prefetch for the next plane: phi plane z+3 into the slot of z-2, ring of z+2
-            async_phi_plane<L, BY>(P, phi_n, fslot(z + 3), x0, y0, z + 3, inside2);
+            async_phi_plane<L, BY, BX>(P, phi_n, fslot(z + 3), x0, y0, z + 3, inside2);
             fetch_ring(z + 2);
         }
         cp_async_commit();
@@ -679,7 +668,7 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
         ingredients(islot(z + 1), fslot(z), fslot(z + 1), fslot(z + 2), z + 1);
         __syncthreads();
         if (active_xy)
-            pull_combine<L, SP, BY, IS_PHI, WALLS>(K, C, fout, sing + islot(z - 1) * G::P1,
+            pull_combine<L, SP, BY, BX, IS_PHI, WALLS>(K, C, fout, sing + islot(z - 1) * G::P1,
                                                    sing + islot(z) * G::P1, sing + islot(z + 1) * G::P1,
                                                    fslot(z - 1), fslot(z), fslot(z + 1), sA + islot(z) * G::P1,
                                                    phi_np1, moment_out, st, macc);
@@ -688,9 +677,9 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
     if (!IS_PHI && mass_partials) block_mass_out<G::NT>(macc, mass_partials, mass_slot);
 }
 
-template <class L, class SP, int BY, int ZCH>
+template <class L, class SP, int BY, int ZCH, int BX = 32>
 constexpr size_t march_smem(bool is_phi) {
-    using G = Geo<L, BY>;
+    using G = Geo<L, BY, BX>;
     using R = typename SP::real;
     return sizeof(V4<R>) * G::NING * G::P1 + sizeof(R) * G::NPHI * G::P2 + sizeof(R) * 2 * G::P1 +
            (is_phi ? sizeof(R) * G::NING * G::P1 : sizeof(R) * 2 * G::P1);
@@ -698,23 +687,23 @@ constexpr size_t march_smem(bool is_phi) {
 
 // ---- the two step kernels ----------------------------------------------------------
 
-template <class L, class SP, int BY, int ZCH, int MINB, bool WALLS>
-__global__ void __launch_bounds__(32 * BY, MINB)
+template <class L, class SP, int BY, int ZCH, int MINB, bool WALLS, int BX = 32>
+__global__ void __launch_bounds__(BX * BY, MINB)
 k_phi_step(const KParams K, const typename SP::store_t* __restrict__ gin,
            typename SP::store_t* __restrict__ gout, const typename SP::real* __restrict__ phi_n,
            const typename SP::real* __restrict__ c_n, typename SP::real* __restrict__ phi_np1) {
-    march<L, SP, BY, ZCH, true, WALLS>(K, gin, gout, phi_n, nullptr, c_n, phi_np1, nullptr,
-                                       blockIdx.x * 32, blockIdx.y * BY, blockIdx.z * ZCH, 0);
+    march<L, SP, BY, ZCH, true, WALLS, BX>(K, gin, gout, phi_n, nullptr, c_n, phi_np1, nullptr,
+                                       blockIdx.x * BX, blockIdx.y * BY, blockIdx.z * ZCH, 0);
 }
 
-template <class L, class SP, int BY, int ZCH, int MINB, bool WALLS>
-__global__ void __launch_bounds__(32 * BY, MINB)
+template <class L, class SP, int BY, int ZCH, int MINB, bool WALLS, int BX = 32>
+__global__ void __launch_bounds__(BX * BY, MINB)
 k_c_step(const KParams K, const typename SP::store_t* __restrict__ hin,
          typename SP::store_t* __restrict__ hout, const typename SP::real* __restrict__ phi_n,
          const typename SP::real* __restrict__ phi_np1, const typename SP::real* __restrict__ c_n,
          typename SP::real* __restrict__ c_np1, double* __restrict__ mass_partials) {
-    march<L, SP, BY, ZCH, false, WALLS>(K, hin, hout, phi_n, phi_np1, c_n, c_np1, mass_partials,
-                                        blockIdx.x * 32, blockIdx.y * BY, blockIdx.z * ZCH,
+    march<L, SP, BY, ZCH, false, WALLS, BX>(K, hin, hout, phi_n, phi_np1, c_n, c_np1, mass_partials,
+                                        blockIdx.x * BX, blockIdx.y * BY, blockIdx.z * ZCH,
                                         blockIdx.x + gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z));
 }
 

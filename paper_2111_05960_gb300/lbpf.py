@@ -81,6 +81,8 @@ def load() -> ctypes.CDLL:
         "lbpf_batch_get_fields": [_vp, ctypes.c_int32, _vp, _vp, _vp, ctypes.c_int32],
         "lbpf_batch_solute_mass": [_vp, _dp],
         "lbpf_adjoint_step": [_vp, _vp, _vp, _vp, _vp, ctypes.c_int32, _dp],
+        "lbpf_batch_tile": [_vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32), _dp],
+        "lbpf_batch_set_tile": [_vp, ctypes.c_int32, ctypes.c_int32],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -98,7 +100,7 @@ def exported_symbols():
             "lbpf_get_fields", "lbpf_get_populations", "lbpf_get_step", "lbpf_destroy",
             "lbpf_last_error", "lbpf_lattice_info", "lbpf_mass_noalloc", "lbpf_solute_mass",
             "lbpf_create_batch", "lbpf_batch_get_fields", "lbpf_batch_solute_mass",
-            "lbpf_adjoint_step"]
+            "lbpf_adjoint_step", "lbpf_batch_tile", "lbpf_batch_set_tile"]
 
 
 def _check(status: int, ctx=None):
@@ -205,6 +207,21 @@ def lbpf_batch_solute_mass(ctx, n: int) -> np.ndarray:
     out = np.zeros(n)
     _check(load().lbpf_batch_solute_mass(ctx, out.ctypes.data_as(_dp)), ctx)
     return out
+
+
+BATCH_TILES = ((64, 16), (64, 32), (128, 16), (128, 32), (256, 16))
+
+
+def lbpf_batch_tile(ctx):
+    """((tile_x, tile_rows) in use, ms per step of each shape in BATCH_TILES)."""
+    tx, tr = ctypes.c_int32(), ctypes.c_int32()
+    ms = np.zeros(len(BATCH_TILES))
+    _check(load().lbpf_batch_tile(ctx, ctypes.byref(tx), ctypes.byref(tr), ms.ctypes.data_as(_dp)))
+    return (tx.value, tr.value), ms
+
+
+def lbpf_batch_set_tile(ctx, tile_x: int, tile_rows: int) -> None:
+    _check(load().lbpf_batch_set_tile(ctx, int(tile_x), int(tile_rows)), ctx)
 
 
 NOALLOC_MAX_ELEMENTS = 67108864
@@ -357,6 +374,12 @@ class BatchSimulation:
 
     def solute_masses(self):
         return lbpf_batch_solute_mass(self.ctx, self.n)
+
+    def tile(self):
+        return lbpf_batch_tile(self.ctx)
+
+    def set_tile(self, tile_x, tile_rows):
+        lbpf_batch_set_tile(self.ctx, tile_x, tile_rows)
 
     def close(self):
         if self.ctx:

@@ -98,3 +98,35 @@ def test_batch_of_the_sweep_workload_runs():
         assert np.all(np.isfinite(phi)) and np.all(np.isfinite(c))
     b.close()
     assert np.max(np.abs(m1 - m0) / m0) < 1e-5
+
+
+def test_every_tile_shape_gives_the_same_bits():
+    # the tile shape changes the schedule only: each node's arithmetic is the same
+    inst = _mixed_instances()
+    ref = None
+    for tile in L.BATCH_TILES:
+        b = L.BatchSimulation([m for m, _, _ in inst], [p for _, p, _ in inst], [c for _, _, c in inst],
+                              precision="fp32")
+        b.set_tile(*tile)
+        assert b.tile()[0] == tile
+        b.step(7)
+        out = [b.fields(i)[:2] for i in range(b.n)]
+        b.close()
+        if ref is None:
+            ref = out
+        for (pa, ca), (pb, cb) in zip(out, ref):
+            assert np.array_equal(pa, pb) and np.array_equal(ca, cb), tile
+
+
+def test_autotuner_times_every_shape_and_keeps_the_fastest():
+    inst = _mixed_instances()
+    b = L.BatchSimulation([m for m, _, _ in inst], [p for _, p, _ in inst], [c for _, _, c in inst],
+                          precision="fp32")
+    tile, ms = b.tile()
+    with pytest.raises(L.LbpfError) as ei:
+        b.set_tile(48, 8)
+    b.close()
+    assert ei.value.status == L.LBPF_EINVAL
+    assert tile in L.BATCH_TILES
+    assert np.all(ms > 0)
+    assert ms[L.BATCH_TILES.index(tile)] == ms.min()
