@@ -65,10 +65,14 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_hash() -> str:
+# sources that define the forward step kernels and their tile shapes
+STEP_SOURCES = ("lattice.cuh", "step_kernels.cuh", "lbpf.cu")
+
+
+def kernel_source_hash(files=STEP_SOURCES) -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2111_05960_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in files:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
