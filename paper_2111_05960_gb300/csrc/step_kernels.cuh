@@ -253,29 +253,66 @@ __device__ __forceinline__ void cp_async(R* smem_dst, const R* gsrc) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// Start the copy of one phi plane (global z index zg, possibly outside) with its
-// 2-node halo (wrapped or mirrored).
-template <class L, int BY, int BX, typename R>
-__device__ __forceinline__ void async_phi_plane(const StepParams& P, const R* __restrict__ phi, R* dst,
-                                                int x0, int y0, int zg, bool inside2) {
-    using G = Geo<L, BY, BX>;
-    const int tid = threadIdx.x + G::BX * threadIdx.y;
-    const int gz = (L::D == 3) ? map_coord(zg, P.nz, P.bc[2]) : 0;
-    const R* src = phi + (long long)gz * P.nx * P.ny;
-    constexpr int IT = (G::P2 + G::NT - 1) / G::NT;
+// In-plane offsets (y nx + x, wrapped on periodic axes, mirrored at walls) of
+// the window elements this thread copies: the phi plane with its 2-node halo
+// (o2) and the 1-node ring (o1).  They are the same for every plane of a
+// march, so they are computed once per block and each plane's copy costs one
+// add per element.
+template <class G>
+struct HaloOffsets {
+    static constexpr int IT2 = (G::P2 + G::NT - 1) / G::NT, IT1 = (G::P1 + G::NT - 1) / G::NT;
+    int o2[IT2];
+    int o1[IT1];
+    __device__ __forceinline__ void init(const StepParams& P, int x0, int y0, bool inside2, bool inside1) {
+        const int tid = threadIdx.x + G::BX * threadIdx.y;
 #pragma unroll
-    for (int it = 0; it < IT; ++it) {
-        const int s = tid + it * G::NT;
-        if (s < G::P2) {
+        for (int it = 0; it < IT2; ++it) {
+            const int s = tid + it * G::NT;
             const int ly = s / G::X2, lx = s - ly * G::X2;
             int gx = x0 + lx - 2, gy = y0 + ly - G::OY2;
             if (!inside2) {
                 gx = map_coord(gx, P.nx, P.bc[0]);
                 gy = map_coord(gy, P.ny, P.bc[1]);
             }
-            cp_async(dst + s, src + (long long)gy * P.nx + gx);
+            o2[it] = s < G::P2 ? gy * P.nx + gx : 0;
+        }
+#pragma unroll
+        for (int it = 0; it < IT1; ++it) {
+            const int s = tid + it * G::NT;
+            const int ly = s / G::X1, lx = s - ly * G::X1;
+            int gx = x0 + lx - 1, gy = y0 + ly - G::OY1;
+            if (!inside1) {
+                gx = wrap1(gx, P.nx, P.bc[0]);
+                gy = wrap1(gy, P.ny, P.bc[1]);
+            }
+            o1[it] = s < G::P1 ? gy * P.nx + gx : 0;
         }
     }
+};
+
+// Start the copy of one phi plane (global z index zg, possibly outside) with its
+// 2-node halo.
+template <class L, class G, typename R>
+__device__ __forceinline__ void async_phi_plane(const StepParams& P, const R* __restrict__ phi, R* dst, int zg,
+                                                const HaloOffsets<G>& H) {
+    const int tid = threadIdx.x + G::BX * threadIdx.y;
+    const int gz = (L::D == 3) ? map_coord(zg, P.nz, P.bc[2]) : 0;
+    const R* src = phi + (long long)gz * P.nx * P.ny;
+#pragma unroll
+    for (int it = 0; it < HaloOffsets<G>::IT2; ++it)
+        if (tid + it * G::NT < G::P2) cp_async(dst + tid + it * G::NT, src + H.o2[it]);
+}
+
+// Start the copy of a field on the 1-node ring of plane zg into shared memory.
+template <class L, class G, typename R>
+__device__ __forceinline__ void async_ring(const StepParams& P, const R* __restrict__ f, R* dst, int zg,
+                                           const HaloOffsets<G>& H) {
+    const int tid = threadIdx.x + G::BX * threadIdx.y;
+    const int gz = (L::D == 3) ? map_coord(zg, P.nz, P.bc[2]) : 0;
+    const R* src = f + (long long)gz * P.nx * P.ny;
+#pragma unroll
+    for (int it = 0; it < HaloOffsets<G>::IT1; ++it)
+        if (tid + it * G::NT < G::P1) cp_async(dst + tid + it * G::NT, src + H.o1[it]);
 }
 
 // grad(phi) by directional derivatives (Eq. DerivDirec_Grad, Eq. Grad) at offset c
@@ -301,36 +338,6 @@ __device__ __forceinline__ void plane_gradient(const R* pm, const R* p0, const R
         if (L::D == 3) {
             if (L::ez(k) > 0) gz += cw * dk;
             if (L::ez(k) < 0) gz -= cw * dk;
-        }
-    }
-}
-
-// Linear index of the ring node (lx, ly) of plane zg (1-node ring, maybe outside).
-template <class L, int BY, int BX>
-__device__ __forceinline__ long long ring_index(const StepParams& P, int x0, int y0, int lx, int ly, int gz,
-                                                bool inside1) {
-    int gx = x0 + lx - 1, gy = y0 + ly - Geo<L, BY, BX>::OY1;
-    if (!inside1) {
-        gx = wrap1(gx, P.nx, P.bc[0]);
-        gy = wrap1(gy, P.ny, P.bc[1]);
-    }
-    return ((long long)gz * P.ny + gy) * P.nx + gx;
-}
-
-// Start the copy of a field on the 1-node ring of plane zg into shared memory.
-template <class L, int BY, int BX, typename R>
-__device__ __forceinline__ void async_ring(const StepParams& P, const R* __restrict__ f, R* dst, int x0, int y0,
-                                           int zg, bool inside1) {
-    using G = Geo<L, BY, BX>;
-    const int tid = threadIdx.x + G::BX * threadIdx.y;
-    const int gz = (L::D == 3) ? map_coord(zg, P.nz, P.bc[2]) : 0;
-    constexpr int IT = (G::P1 + G::NT - 1) / G::NT;
-#pragma unroll
-    for (int it = 0; it < IT; ++it) {
-        const int s = tid + it * G::NT;
-        if (s < G::P1) {
-            const int ly = s / G::X1, lx = s - ly * G::X1;
-            cp_async(dst + s, f + ring_index<L, BY, BX>(P, x0, y0, lx, ly, gz, inside1));
         }
     }
 }
@@ -618,10 +625,12 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
     MassAcc<R> macc{R(0), R(0)};
 
     // the ring inputs of plane zg go to stage buffer zg & 1
+    HaloOffsets<G> halo;
+    halo.init(P, x0, y0, inside2, inside1);
     auto fetch_ring = [&](int zg) {
         const int b = zg & 1;
-        async_ring<L, BY, BX>(P, c_n, cst + b * G::P1, x0, y0, zg, inside1);
-        if (!IS_PHI) async_ring<L, BY, BX>(P, phi_np1, pst + b * G::P1, x0, y0, zg, inside1);
+        async_ring<L, G>(P, c_n, cst + b * G::P1, zg, halo);
+        if (!IS_PHI) async_ring<L, G>(P, phi_np1, pst + b * G::P1, zg, halo);
     };
     auto ingredients = [&](int slot_i, const R* pm, const R* p0, const R* pp, int zg) {
         const int b = zg & 1;
@@ -640,7 +649,7 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
     auto fslot = [&](int zg) { return sphi + ((zg - z0 + 2 + 5 * ZCH) % 5) * G::P2; };
     auto islot = [&](int zg) { return (zg - z0 + 1 + 3 * ZCH) % 3; };
 
-    for (int zg = z0 - 2; zg <= z0 + 1; ++zg) async_phi_plane<L, BY, BX>(P, phi_n, fslot(zg), x0, y0, zg, inside2);
+    for (int zg = z0 - 2; zg <= z0 + 1; ++zg) async_phi_plane<L, G>(P, phi_n, fslot(zg), zg, halo);
     fetch_ring(z0 - 1);
     cp_async_commit();
     cp_async_wait_all();
@@ -652,7 +661,7 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
     cp_async_wait_all();
     __syncthreads();
     ingredients(islot(z0), fslot(z0 - 1), fslot(z0), fslot(z0 + 1), z0);
-    async_phi_plane<L, BY, BX>(P, phi_n, fslot(z0 + 2), x0, y0, z0 + 2, inside2);
+    async_phi_plane<L, G>(P, phi_n, fslot(z0 + 2), z0 + 2, halo);
     fetch_ring(z0 + 1);
     cp_async_commit();
     for (int z = z0; z < z1; ++z) {
@@ -660,7 +669,7 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
         __syncthreads();                 // ... for every thread; pull(z-1) is done everywhere
         if (z + 1 < z1) {
             // prefetch for the next plane: phi plane z+3 into the slot of z-2, ring of z+2
-            async_phi_plane<L, BY, BX>(P, phi_n, fslot(z + 3), x0, y0, z + 3, inside2);
+            async_phi_plane<L, G>(P, phi_n, fslot(z + 3), z + 3, halo);
             fetch_ring(z + 2);
         }
         cp_async_commit();
