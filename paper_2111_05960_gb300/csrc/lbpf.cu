@@ -78,14 +78,23 @@ namespace {
 #ifndef LBPF_MINB2
 #define LBPF_MINB2 6
 #endif
+// 3-D, FP32 arithmetic (FP32 and 16-bit storage): 32 x 4 tiles, 32 planes,
+// 6 blocks per SM; FP64: 32 x 8 tiles, 16 planes, 2 blocks per SM (register
+// bound).  Chosen by timing the 256^3 porous step on GB300.
 #ifndef LBPF_BY3
-#define LBPF_BY3 8
+#define LBPF_BY3 4
 #endif
 #ifndef LBPF_ZCH3
-#define LBPF_ZCH3 16
+#define LBPF_ZCH3 32
 #endif
 #ifndef LBPF_MINB3
-#define LBPF_MINB3 3
+#define LBPF_MINB3 6
+#endif
+#ifndef LBPF_BY3_F64
+#define LBPF_BY3_F64 8
+#endif
+#ifndef LBPF_ZCH3_F64
+#define LBPF_ZCH3_F64 16
 #endif
 #ifndef LBPF_MINB3_F64
 #define LBPF_MINB3_F64 2
@@ -94,30 +103,31 @@ namespace {
 // value near 1, so that each node's rounding is ~1% of the increment.
 constexpr double kCorrDelta = 1e-5;
 
-template <class L>
+template <class L, bool F64>
 struct TileCfg;
-template <>
-struct TileCfg<D2Q9> {
+template <bool F64>
+struct TileCfg<D2Q9, F64> {
     using ML = D2Q9R;
     static constexpr int BX = LBPF_BX2, BY = 1, ZCH = LBPF_YCH2, MINB = LBPF_MINB2;
 };
 template <>
-struct TileCfg<D3Q19> {
+struct TileCfg<D3Q19, false> {
     using ML = D3Q19;
     static constexpr int BX = 32, BY = LBPF_BY3, ZCH = LBPF_ZCH3, MINB = LBPF_MINB3;
 };
-template <class L, class SP>
-constexpr int min_blocks() {
-    return (L::D == 3 && sizeof(typename SP::real) == 8) ? LBPF_MINB3_F64 : TileCfg<L>::MINB;
-}
+template <>
+struct TileCfg<D3Q19, true> {
+    using ML = D3Q19;
+    static constexpr int BX = 32, BY = LBPF_BY3_F64, ZCH = LBPF_ZCH3_F64, MINB = LBPF_MINB3_F64;
+};
 
 template <class L, class SP>
 struct Impl {
     using R = typename SP::real;
     using S = typename SP::store_t;
-    using ML = typename TileCfg<L>::ML;     // the lattice as the marching kernels see it
-    static constexpr int BX = TileCfg<L>::BX, BY = TileCfg<L>::BY, ZCH = TileCfg<L>::ZCH,
-                         MINB = min_blocks<L, SP>();
+    using T = TileCfg<L, sizeof(R) == 8>;
+    using ML = typename T::ML;              // the lattice as the marching kernels see it
+    static constexpr int BX = T::BX, BY = T::BY, ZCH = T::ZCH, MINB = T::MINB;
     static constexpr size_t smem_phi = march_smem<ML, SP, BY, ZCH, BX>(true);
     static constexpr size_t smem_c = march_smem<ML, SP, BY, ZCH, BX>(false);
     template <bool W>

@@ -255,7 +255,8 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 // In-plane offsets (y nx + x, wrapped on periodic axes, mirrored at walls) of
 // the window elements this thread copies: the phi plane with its 2-node halo
-// (o2) and the 1-node ring (o1).  They are the same for every plane of a
+// (o2) and the 1-node ring (o1), and the phi-window index of each ring node it
+// computes ingredients for (c2).  They are the same for every plane of a
 // march, so they are computed once per block and each plane's copy costs one
 // add per element.
 template <class G>
@@ -263,6 +264,7 @@ struct HaloOffsets {
     static constexpr int IT2 = (G::P2 + G::NT - 1) / G::NT, IT1 = (G::P1 + G::NT - 1) / G::NT;
     int o2[IT2];
     int o1[IT1];
+    int c2[IT1];
     __device__ __forceinline__ void init(const StepParams& P, int x0, int y0, bool inside2, bool inside1) {
         const int tid = threadIdx.x + G::BX * threadIdx.y;
 #pragma unroll
@@ -286,6 +288,7 @@ struct HaloOffsets {
                 gy = wrap1(gy, P.ny, P.bc[1]);
             }
             o1[it] = s < G::P1 ? gy * P.nx + gx : 0;
+            c2[it] = (ly + G::OY2 - G::OY1) * G::X2 + (lx + 1);
         }
     }
 };
@@ -346,7 +349,8 @@ __device__ __forceinline__ void plane_gradient(const R* pm, const R* p0, const R
 // A = G^st + G^dw.
 template <class L, int BY, int BX, typename R>
 __device__ __forceinline__ void phi_ingredients(const StepParams& P, const Coef<R>& C, const R* cst,
-                                                const R* pm, const R* p0, const R* pp, V4<R>* ing, R* sA) {
+                                                const R* pm, const R* p0, const R* pp, V4<R>* ing, R* sA,
+                                                const HaloOffsets<Geo<L, BY, BX>>& H) {
     using G = Geo<L, BY, BX>;
     const int tid = threadIdx.x + G::BX * threadIdx.y;
     const R half_src = R(1) - R(0.5) * C.omg;
@@ -355,8 +359,7 @@ __device__ __forceinline__ void phi_ingredients(const StepParams& P, const Coef<
     for (int it = 0; it < IT; ++it) {
         const int s = tid + it * G::NT;
         if (s >= G::P1) break;
-        const int ly = s / G::X1, lx = s - ly * G::X1;
-        const int c2 = (ly + G::OY2 - G::OY1) * G::X2 + (lx + 1);
+        const int c2 = H.c2[it];
         const R ph = p0[c2];
         const R mu = closure_mu(C, ph, cst[s]);
         const R A = g_isotropic(C, ph, mu);
@@ -380,7 +383,8 @@ __device__ __forceinline__ void phi_ingredients(const StepParams& P, const Coef<
 // beta_h = (1 - w_h/2) gamma (mu D' grad phi + j_at).
 template <class L, int BY, int BX, typename R>
 __device__ __forceinline__ void c_ingredients(const StepParams& P, const Coef<R>& C, const R* cst, const R* pst,
-                                              const R* pm, const R* p0, const R* pp, V4<R>* ing) {
+                                              const R* pm, const R* p0, const R* pp, V4<R>* ing,
+                                              const HaloOffsets<Geo<L, BY, BX>>& H) {
     using G = Geo<L, BY, BX>;
     const int tid = threadIdx.x + G::BX * threadIdx.y;
     constexpr int IT = (G::P1 + G::NT - 1) / G::NT;
@@ -388,8 +392,7 @@ __device__ __forceinline__ void c_ingredients(const StepParams& P, const Coef<R>
     for (int it = 0; it < IT; ++it) {
         const int s = tid + it * G::NT;
         if (s >= G::P1) break;
-        const int ly = s / G::X1, lx = s - ly * G::X1;
-        const int c2 = (ly + G::OY2 - G::OY1) * G::X2 + (lx + 1);
+        const int c2 = H.c2[it];
         const R ph = p0[c2];
         const R dphi = pst[s] - ph;                        // explicit Euler dphi/dt
         const R mu = closure_mu(C, ph, cst[s]);
@@ -635,9 +638,11 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
     auto ingredients = [&](int slot_i, const R* pm, const R* p0, const R* pp, int zg) {
         const int b = zg & 1;
         if (IS_PHI)
-            phi_ingredients<L, BY, BX>(P, C, cst + b * G::P1, pm, p0, pp, sing + slot_i * G::P1, sA + slot_i * G::P1);
+            phi_ingredients<L, BY, BX>(P, C, cst + b * G::P1, pm, p0, pp, sing + slot_i * G::P1, sA + slot_i * G::P1,
+                                       halo);
         else
-            c_ingredients<L, BY, BX>(P, C, cst + b * G::P1, pst + b * G::P1, pm, p0, pp, sing + slot_i * G::P1);
+            c_ingredients<L, BY, BX>(P, C, cst + b * G::P1, pst + b * G::P1, pm, p0, pp, sing + slot_i * G::P1,
+                                     halo);
     };
 
     static_assert(L::D == 3, "2-D domains march through the D2Q9R view");
