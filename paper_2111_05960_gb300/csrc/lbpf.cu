@@ -76,7 +76,10 @@ namespace {
 #define LBPF_YCH2 16
 #endif
 #ifndef LBPF_MINB2
-#define LBPF_MINB2 6
+#define LBPF_MINB2 8
+#endif
+#ifndef LBPF_MINB2_F64
+#define LBPF_MINB2_F64 6
 #endif
 // 3-D, FP32 arithmetic (FP32 and 16-bit storage): 32 x 4 tiles, 32 planes,
 // 6 blocks per SM; FP64: 32 x 8 tiles, 16 planes, 2 blocks per SM (register
@@ -108,7 +111,7 @@ struct TileCfg;
 template <bool F64>
 struct TileCfg<D2Q9, F64> {
     using ML = D2Q9R;
-    static constexpr int BX = LBPF_BX2, BY = 1, ZCH = LBPF_YCH2, MINB = LBPF_MINB2;
+    static constexpr int BX = LBPF_BX2, BY = 1, ZCH = LBPF_YCH2, MINB = F64 ? LBPF_MINB2_F64 : LBPF_MINB2;
 };
 template <>
 struct TileCfg<D3Q19, false> {
