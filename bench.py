@@ -65,8 +65,10 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-# sources that define the forward step kernels and their tile shapes
-STEP_SOURCES = ("lattice.cuh", "step_kernels.cuh", "lbpf.cu")
+# sources that define the 3-D step kernels, and the lines of lbpf.cu that fix
+# their FP32 tile shape
+STEP_SOURCES = ("lattice.cuh", "step_kernels.cuh")
+STEP_TILE_MACROS = ("LBPF_BY3", "LBPF_ZCH3", "LBPF_MINB3")
 
 
 def kernel_source_hash(files=STEP_SOURCES) -> str:
@@ -75,6 +77,10 @@ def kernel_source_hash(files=STEP_SOURCES) -> str:
     for f in files:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
+    with open(os.path.join(csrc, "lbpf.cu")) as fh:
+        for line in fh:
+            if line.startswith("#define") and line.split()[1] in STEP_TILE_MACROS:
+                h.update(line.encode())
     return h.hexdigest()[:16]
 
 
