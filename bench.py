@@ -71,7 +71,7 @@ STEP_SOURCES = ("lattice.cuh", "step_kernels.cuh")
 STEP_TILE_MACROS = ("LBPF_BY3", "LBPF_ZCH3", "LBPF_MINB3")
 
 
-def kernel_source_hash(files=STEP_SOURCES) -> str:
+def kernel_source_hash(files=STEP_SOURCES, macros=STEP_TILE_MACROS) -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2111_05960_gb300", "csrc")
     for f in files:
@@ -79,7 +79,7 @@ def kernel_source_hash(files=STEP_SOURCES) -> str:
             h.update(fh.read())
     with open(os.path.join(csrc, "lbpf.cu")) as fh:
         for line in fh:
-            if line.startswith("#define") and line.split()[1] in STEP_TILE_MACROS:
+            if line.startswith("#define") and line.split()[1] in macros:
                 h.update(line.encode())
     return h.hexdigest()[:16]
 
@@ -97,6 +97,29 @@ def ncu_traffic(kernel: str, workload: str):
         return float(e["bytes_per_launch"])
     except Exception:
         return None
+
+
+def fp64_roofline(stream, nodes, ms_per_step, workload):
+    """The FP64 step against the FP64 pipe of this GPU.  Every FP64 add, multiply
+    or FMA occupies one FP64 issue slot, so the step's FP64 instructions per
+    node (committed ncu count, profiles/fp64_flops.json, while the step-kernel
+    sources match) are counted as FMAs (2 flops each) and compared with the FMA
+    rate lbpf_fp64_fma_rate measures; arithmetic flops are reported beside."""
+    from paper_2111_05960_gb300 import lbpf as L
+    peak = L.lbpf_fp64_fma_rate(stream.cuda_stream)
+    out = {"bound": "alu", "peak": peak, "unit": "TFLOP/s", "peak_source": "measured (lbpf_fp64_fma_rate)",
+           "counting": "FP64 pipe instructions x 2 (FMA-equivalent)", "achieved": None, "frac": None}
+    try:
+        with open(os.path.join(ROOT, "profiles", "fp64_flops.json")) as f:
+            d = json.load(f)
+        if d.get("source_hash") == kernel_source_hash(STEP_SOURCES, ("LBPF_BY3_F64", "LBPF_ZCH3_F64", "LBPF_MINB3_F64")):
+            ipn = float(d["fp64_instructions_per_node"])
+            ach = 2.0 * ipn * nodes / (ms_per_step * 1e-3) / 1e12
+            out.update({"achieved": ach, "frac": ach / peak, "fp64_instructions_per_node": ipn,
+                        "arithmetic_tflops": float(d["flops_per_node"]) * nodes / (ms_per_step * 1e-3) / 1e12})
+    except Exception:
+        pass
+    return out
 
 
 class ClockSampler:
@@ -249,8 +272,31 @@ def adjoint_measurement(args, stream, hbm, fwd_bytes_per_node):
                     "reverse kernels = sweep - forward (the replay is the forward's kernels)"}
 
 
-def cpu_baseline(model, phi0, c0, budget_s=12.0):
-    """The FP64 oracle, as it stands, on a z-slab of the same medium (periodic)."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        import subprocess
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k = line.split(":")[0].strip().lower()
+                if k in ("model name", "cpu model", "hardware"):
+                    return line.split(":", 1)[1].strip()
+        import platform
+        return platform.machine()
+    except Exception:
+        return "unknown"
+
+
+def cpu_baseline(model, phi0, c0, budget_s=12.0, single_s=3.0):
+    """The FP64 oracle, as it stands, on a z-slab of the same medium (periodic):
+    on all host cores (OpenMP) for ~budget_s, and on one core for ~single_s."""
     import oracle as O
     names = O.OracleParams.__dataclass_fields__
     nz = 16
@@ -258,18 +304,26 @@ def cpu_baseline(model, phi0, c0, budget_s=12.0):
     sub_c = np.ascontiguousarray(c0[:nz])
     p = O.OracleParams(**{k: getattr(model, k) for k in names})
     p.nz = nz
-    threads = O.Oracle.threads()
-    o = O.Oracle(p, sub_phi, sub_c)
-    t = time.perf_counter()
-    o.step(1)
-    one = time.perf_counter() - t
-    steps = max(1, int(budget_s / max(one, 1e-3)))
-    t = time.perf_counter()
-    o.step(steps)
-    el = time.perf_counter() - t
     nodes = p.nx * p.ny * nz
+
+    def timed(budget):
+        o = O.Oracle(p, sub_phi, sub_c)
+        t = time.perf_counter()
+        o.step(1)
+        one = time.perf_counter() - t
+        steps = max(1, int(budget / max(one, 1e-3)))
+        t = time.perf_counter()
+        o.step(steps)
+        return steps, time.perf_counter() - t
+
+    threads = O.Oracle.threads()
+    steps, el = timed(budget_s)
+    O.Oracle.set_threads(1)
+    steps1, el1 = timed(single_s)
+    O.Oracle.set_threads(threads)
     return {"value": nodes * steps / el / 1e6, "unit": "MLUPS", "cores": threads, "kind": "oracle",
-            "sample": "%dx%dx%d z-slab of the 256^3 medium, %d FP64 steps, %.1f s" % (p.nx, p.ny, nz, steps, el)}
+            "sample": "%dx%dx%d z-slab of the 256^3 medium, %d FP64 steps, %.1f s" % (p.nx, p.ny, nz, steps, el),
+            "single_core_value": nodes * steps1 / el1 / 1e6, "cpu_model": cpu_model(), "nproc": os.cpu_count()}
 
 
 def run_reference(args):
@@ -388,7 +442,8 @@ def run_ours(args):
         ms64 = a.elapsed_time(b) / args.fp64_steps
         sim64.close()
         extra["fp64_forward"] = {"ms_per_step": ms64, "mlups": N / (ms64 * 1e-3) / 1e6,
-                                 "fp32_speedup": ms64 / ms_per_step}
+                                 "fp32_speedup": ms64 / ms_per_step,
+                                 "roofline": fp64_roofline(stream, N, ms64, wl.replace("_fp32", "_fp64"))}
 
     batch = None
     if args.batch_steps > 0 and prec == "fp32":

@@ -169,6 +169,15 @@ lbpf_status lbpf_get_populations(lbpf_ctx *ctx, double *g, double *h, int32_t pt
  * Synchronises. */
 lbpf_status lbpf_step_timed(lbpf_ctx *ctx, int64_t nsteps, double *kernel_ms);
 
+/* Measured FP64 FMA throughput of the current device in TFLOP/s (*tflops),
+ * from a kernel of independent FMA chains on every SM (about a second of
+ * work at 1 TFLOP/s scale), timed with CUDA events on cuda_stream (NULL =
+ * default stream); synchronises it.  The FP64 step is bound by FP64
+ * arithmetic rather than by memory on GPUs with a small FP64 rate, and this
+ * is its roofline denominator.  The paper has no counterpart.
+ * Errors: EINVAL (tflops NULL), ECUDA. */
+lbpf_status lbpf_fp64_fma_rate(void *cuda_stream, double *tflops);
+
 /* Lattice table of the population ordering used by lbpf_get_populations:
  * *q = 9 or 19; e (optional, int32 [q][3]) the link vectors; w (optional,
  * [q]) the weights.  D2Q9 follows Sec. 3.1 (e0 = 0, e1..e4 axis links

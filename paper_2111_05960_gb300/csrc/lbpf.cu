@@ -438,6 +438,28 @@ void launch_mass(lbpf_ctx* ctx) {
 
 }  // namespace
 
+// ---- FP64 arithmetic rate (the ALU roofline of the FP64 step) ---------------------
+
+constexpr int kFmaThreads = 256, kFmaChains = 8;
+__device__ double g_fma_sink;
+
+// kFmaChains independent FMA chains per thread, so the FP64 pipe, not the
+// dependency latency, sets the rate; the result is kept so nothing is elided.
+__global__ void __launch_bounds__(kFmaThreads) k_fp64_fma(int iters, double seed) {
+    double a[kFmaChains];
+#pragma unroll
+    for (int j = 0; j < kFmaChains; ++j) a[j] = seed + 1e-3 * (threadIdx.x + j);
+    const double m = 0.999999, c = 1e-7;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int j = 0; j < kFmaChains; ++j) a[j] = fma(a[j], m, c);
+    }
+    double t = 0.0;
+#pragma unroll
+    for (int j = 0; j < kFmaChains; ++j) t += a[j];
+    if (t == -1.0) g_fma_sink = t;      // never true; keeps the chains alive
+}
+
 // ==== C ABI ======================================================================
 
 extern "C" {
@@ -722,6 +744,33 @@ lbpf_status lbpf_destroy(lbpf_ctx* ctx) {
 
 const char* lbpf_last_error(const lbpf_ctx* ctx) {
     return ctx ? ctx->err.c_str() : g_thread_error.c_str();
+}
+
+lbpf_status lbpf_fp64_fma_rate(void* cuda_stream, double* tflops) {
+    if (!tflops) return fail(nullptr, LBPF_EINVAL, "tflops is NULL");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int dev = 0, sms = 0;
+    LBPF_CUDA(nullptr, cudaGetDevice(&dev));
+    LBPF_CUDA(nullptr, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = 8 * sms, iters = 1 << 11;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    LBPF_CUDA(nullptr, cudaEventCreate(&e0));
+    cudaError_t e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) { cudaEventDestroy(e0); return cuda_fail(nullptr, e, "cudaEventCreate"); }
+    k_fp64_fma<<<blocks, kFmaThreads, 0, s>>>(iters / 16, 1.0);      // warm-up
+    cudaEventRecord(e0, s);
+    k_fp64_fma<<<blocks, kFmaThreads, 0, s>>>(iters, 1.0);
+    cudaEventRecord(e1, s);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "FP64 rate kernel");
+    const double flops = 2.0 * kFmaChains * (double)iters * blocks * kFmaThreads;
+    *tflops = flops / (ms * 1e-3) / 1e12;
+    return LBPF_OK;
 }
 
 lbpf_status lbpf_lattice_info(int32_t lattice, int32_t* q, int32_t* e, double* w) {

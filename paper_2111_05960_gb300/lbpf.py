@@ -83,6 +83,7 @@ def load() -> ctypes.CDLL:
         "lbpf_adjoint_step": [_vp, _vp, _vp, _vp, _vp, ctypes.c_int32, _dp],
         "lbpf_batch_tile": [_vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32), _dp],
         "lbpf_batch_set_tile": [_vp, ctypes.c_int32, ctypes.c_int32],
+        "lbpf_fp64_fma_rate": [_vp, _dp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -100,7 +101,7 @@ def exported_symbols():
             "lbpf_get_fields", "lbpf_get_populations", "lbpf_get_step", "lbpf_destroy",
             "lbpf_last_error", "lbpf_lattice_info", "lbpf_mass_noalloc", "lbpf_solute_mass",
             "lbpf_create_batch", "lbpf_batch_get_fields", "lbpf_batch_solute_mass",
-            "lbpf_adjoint_step", "lbpf_batch_tile", "lbpf_batch_set_tile"]
+            "lbpf_adjoint_step", "lbpf_batch_tile", "lbpf_batch_set_tile", "lbpf_fp64_fma_rate"]
 
 
 def _check(status: int, ctx=None):
@@ -248,6 +249,13 @@ def lbpf_adjoint_step(ctx, dL_dphi=None, dL_dc=None, dL_dphi0=None, dL_dc0=None,
     _check(load().lbpf_adjoint_step(ctx, _ptr(dL_dphi)[0], _ptr(dL_dc)[0], _ptr(dL_dphi0)[0],
                                     _ptr(dL_dc0)[0], int(ptr_is_device), out.ctypes.data_as(_dp)), ctx)
     return out
+
+
+def lbpf_fp64_fma_rate(cuda_stream=None) -> float:
+    """Measured FP64 FMA throughput of the current device, TFLOP/s."""
+    t = ctypes.c_double()
+    _check(load().lbpf_fp64_fma_rate(cuda_stream or None, ctypes.byref(t)))
+    return t.value
 
 
 def lbpf_lattice_info(lattice: int):

@@ -222,3 +222,10 @@ def test_fp32_mass_held_by_fp64_correction(precision, bound):
         drift.append(abs(mk - m0) / m0)
     sim.close()
     assert max(drift) < bound, drift
+
+
+def test_fp64_fma_rate_is_measured():
+    # the FP64 roofline denominator: a positive, finite rate, stable between calls
+    r = [L.lbpf_fp64_fma_rate() for _ in range(2)]
+    assert all(0.05 < v < 200.0 for v in r), r
+    assert abs(r[0] - r[1]) <= 0.1 * max(r), r
