@@ -55,6 +55,12 @@ constexpr int kAdjBX = 32, kAdjBY = 8, kAdjThreads = kAdjBX * kAdjBY;
 #endif
 template <typename R>
 constexpr int adj_minb() { return sizeof(R) == 8 ? LBPF_ADJ_MINB_F64 : LBPF_ADJ_MINB_F32; }
+// the phi part gathers more per link; its register budget is set on its own
+#ifndef LBPF_ADJ_MINB_G_F32
+#define LBPF_ADJ_MINB_G_F32 LBPF_ADJ_MINB_F32
+#endif
+template <typename R>
+constexpr int adj_minb_g() { return sizeof(R) == 8 ? LBPF_ADJ_MINB_F64 : LBPF_ADJ_MINB_G_F32; }
 // Parameter adjoints, in this order: D_l, tau_g, tau_h, lambda, a (of j_at), D_s.
 constexpr int kAdjParams = 6;
 enum { kPDl = 0, kPTauG = 1, kPTauH = 2, kPLam = 3, kPA = 4, kPDs = 5 };
@@ -386,7 +392,7 @@ k_adj_h(const StepParams P, const AdjCoef<R> C, const R* __restrict__ h, const R
 
 // ---- phi part ---------------------------------------------------------------------
 template <class L, typename R>
-__global__ void __launch_bounds__(kAdjThreads, adj_minb<R>())
+__global__ void __launch_bounds__(kAdjThreads, adj_minb_g<R>())
 k_adj_g(const StepParams P, const AdjCoef<R> C, const R* __restrict__ g, const R* __restrict__ phi,
         const R* __restrict__ c, const R* __restrict__ gb_in, R* __restrict__ gb_out, AdjWork<R> T,
         R* __restrict__ phib_out, R* __restrict__ cb_out, double* __restrict__ pacc, int nblk) {
@@ -400,8 +406,13 @@ k_adj_g(const StepParams P, const AdjCoef<R> C, const R* __restrict__ g, const R
         f.compute(C, phi, c, a);
         PhiSource<L, R> src;
         src.compute(C, f);
-        const R dphib_here = T.dphi[i];
-        const R pt = T.pt[i];                            // adjoint of phi^{n+1} at this node
+        // The work area is read-only in this kernel except for the gradient
+        // adjoint: its reads go through the non-coherent path, so the compiler
+        // may issue them ahead of the gb_out stores (a plain load through the
+        // unqualified AdjWork pointers could alias them and would serialise the
+        // link loop on memory latency).
+        const R dphib_here = __ldg(T.dphi + i);
+        const R pt = __ldg(T.pt + i);                    // adjoint of phi^{n+1} at this node
         // s_k: adjoint of the post-collision population k; phi^{n+1} = sum g' + G/2
         R S0 = R(0), SV[3] = {R(0), R(0), R(0)}, Sneq = R(0);
 #pragma unroll
@@ -409,7 +420,7 @@ k_adj_g(const StepParams P, const AdjCoef<R> C, const R* __restrict__ g, const R
             const long long d = i + nbr_off<L>(a, k);
             const bool wall = (a.walls & out_bits<L>(k)) != 0;
             const R s = wall ? gb_in[(long long)L::opp(k) * N + i] + pt
-                             : gb_in[(long long)k * N + d] + T.pt[d];
+                             : gb_in[(long long)k * N + d] + __ldg(T.pt + d);
             gb_out[(long long)k * N + i] = (R(1) - C.omg) * s;
             Sneq += s * (R(L::w(k)) * f.ph - R(0.5) * src.G(C, f, k) - g[(long long)k * N + i]);
             S0 += R(L::w(k)) * s;
@@ -425,8 +436,8 @@ k_adj_g(const StepParams P, const AdjCoef<R> C, const R* __restrict__ g, const R
         adj_phi_sources<L, R>(C, f, src, Gstb, GbV, phib, mub, nb, pv);
         adj_closure_normal<L, R>(C, f, mub, nb, phib, cb, gradb);
         for (int d = 0; d < 3; ++d) T.grad[d * N + i] += gradb[d];
-        phib_out[i] = T.phi[i] + phib;
-        cb_out[i] = T.c[i] + cb;
+        phib_out[i] = __ldg(T.phi + i) + phib;
+        cb_out[i] = __ldg(T.c + i) + cb;
     }
     adj_param_flush(pv, pacc, nblk);
 }
