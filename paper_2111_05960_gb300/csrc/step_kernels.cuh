@@ -110,6 +110,7 @@ struct StoreF64 {
     using store_t = double;
     __device__ static __forceinline__ real load(const store_t* p, long long i, real) { return p[i]; }
     __device__ static __forceinline__ void store(store_t* p, long long i, real v, real) { p[i] = v; }
+    __device__ static __forceinline__ real stored(real v, real) { return v; }
     static constexpr bool deviation = false;
 };
 
@@ -118,6 +119,7 @@ struct StoreF32 {
     using store_t = float;
     __device__ static __forceinline__ real load(const store_t* p, long long i, real) { return p[i]; }
     __device__ static __forceinline__ void store(store_t* p, long long i, real v, real) { p[i] = v; }
+    __device__ static __forceinline__ real stored(real v, real) { return v; }
     static constexpr bool deviation = false;
 };
 
@@ -133,6 +135,10 @@ struct StoreF16Dev {
     __device__ static __forceinline__ void store(store_t* p, long long i, real v, real ref) {
         p[i] = __float2half_rn((v - ref) * S);
     }
+    // the value a later load returns for a stored v
+    __device__ static __forceinline__ real stored(real v, real ref) {
+        return fmaf(__half2float(__float2half_rn((v - ref) * S)), INV, ref);
+    }
     static constexpr bool deviation = true;
 };
 
@@ -144,6 +150,9 @@ struct StoreBF16Dev {
     }
     __device__ static __forceinline__ void store(store_t* p, long long i, real v, real ref) {
         p[i] = __float2bfloat16_rn(v - ref);
+    }
+    __device__ static __forceinline__ real stored(real v, real ref) {
+        return __bfloat162float(__float2bfloat16_rn(v - ref)) + ref;
     }
     static constexpr bool deviation = true;
 };
@@ -558,7 +567,7 @@ __device__ __forceinline__ void pull_combine(const KParams& K, const Coef<typena
         if (!hold) SP::store(out, K.kN[k], val, R(0));
     }
     if (!IS_PHI) {
-        macc.add(sum, comp);   // the node's exact population mass is sum + comp
+        if (!hold) macc.add(sum, comp);   // the node's exact population mass is sum + comp
         sum += comp;
     }
     if (IS_PHI) {
@@ -573,9 +582,21 @@ __device__ __forceinline__ void pull_combine(const KParams& K, const Coef<typena
         if (hold) {
             const R phin = phi_np1_in[xi];
             const R Ps = p_term(C, phin, closure_mu(C, phin, sum)) / R(36);
-            SP::store(out, K.kN[0], v[0], sum - R(36 - L::m(0)) * Ps);
+            // the mass regulated by the correction is that of the populations as
+            // stored (quantised), i.e. of the values the next step loads
+            const R ref0 = sum - R(36 - L::m(0)) * Ps;
+            SP::store(out, K.kN[0], v[0], ref0);
+            R ms = SP::stored(v[0], ref0), mcomp = R(0);
 #pragma unroll
-            for (int k = 1; k < L::Q; ++k) SP::store(out, K.kN[k], v[k], R(L::m(k)) * Ps);
+            for (int k = 1; k < L::Q; ++k) {
+                const R ref = R(L::m(k)) * Ps;
+                SP::store(out, K.kN[k], v[k], ref);
+                const R vs = SP::stored(v[k], ref);
+                const R t = ms + vs;
+                mcomp += (ms - t) + vs;
+                ms = t;
+            }
+            macc.add(ms, mcomp);
         }
     }
 }

@@ -99,7 +99,10 @@ def test_disc_config_fp64_counter_term_on_and_off():
         assert max(errs.values()) < FP64_TOL, (ct, errs)
 
 
-@pytest.mark.parametrize("precision,tol", [("fp32", 2e-5)])
+# Stated errors of the reduced-precision modes against the FP64 oracle
+# (max |a - b| / max |b|): the 128^2 disc after 200 steps measures 8e-7 (FP32),
+# 1.2e-5 (FP16 deviation storage) and 1.9e-4 (BF16 deviation storage).
+@pytest.mark.parametrize("precision,tol", [("fp32", 2e-5), ("fp16dev", 2e-5), ("bf16dev", 3e-4)])
 def test_reduced_precision_error_against_fp64_oracle(precision, tol):
     m, phi0, c0 = WL.disc_2d(n=128, R=30.0, counter_term=1, equilibrium=False)
     errs = _compare(m, phi0, c0, 200, precision=precision, pops=False)
@@ -202,15 +205,14 @@ def test_solute_mass_matches_oracle_definition():
     assert np.isnan(target)
 
 
-@pytest.mark.parametrize("precision,bound", [("fp32", 1e-10), ("fp16dev", 1e-8), ("bf16dev", 1e-7)])
+@pytest.mark.parametrize("precision,bound", [("fp32", 1e-10), ("fp16dev", 1e-9), ("bf16dev", 1e-9)])
 def test_fp32_mass_held_by_fp64_correction(precision, bound):
     """FP32 rounding drifts the solute by ~1e-9 per step; with the
     FP64 correction every step the exact population mass stays at its initial
-    value to within the FP32 rounding of one step (bound 1e-9 relative over 2000
-    steps, against the 1e-9 target; measured ~1e-12).  16-bit deviation storage
-    regulates the sum it computes; its stored populations differ from that sum
-    by the quantisation of one step, hence the looser bounds (measured ~2e-9 for
-    FP16, ~1e-8 for BF16)."""
+    value to within the FP32 rounding of one step (bound 1e-10 relative over 2000
+    steps; measured ~1e-12).  In the 16-bit deviation modes the composition
+    kernel sums the populations as stored (quantised), so the same loop holds
+    their mass to the 1e-9 target as well."""
     m, phi0, c0 = WL.porous_3d(n=64)
     sim = L.Simulation(m, phi0, c0, precision=precision, mass_every=1)
     m0, target = sim.solute_mass()
@@ -229,3 +231,24 @@ def test_fp64_fma_rate_is_measured():
     r = [L.lbpf_fp64_fma_rate() for _ in range(2)]
     assert all(0.05 < v < 200.0 for v in r), r
     assert abs(r[0] - r[1]) <= 0.1 * max(r), r
+
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 2e-5), ("fp16dev", 2e-5), ("bf16dev", 4e-5)])
+def test_reduced_precision_error_on_porous_medium(precision, tol):
+    """A 48^3 crop of the porous workload, 100 steps with the mass correction,
+    against the FP64 oracle.  With eps_n = 1e-3 the step is well conditioned
+    and the errors are the precision's (measured: FP32 1.4e-5, FP16 1.2e-5,
+    BF16 2.4e-5 in c).  With eps_n = 1e-12 the unit normal turns freely at
+    nodes where grad phi vanishes, and rounding differences there grow to 1.5e-4
+    at a few nodes (their 99.9th percentile stays at 1.1e-5 in FP32)."""
+    import dataclasses
+    m, phi0, c0 = WL.porous_3d(n=48)
+    m = dataclasses.replace(m, eps_n=1e-3)
+    o = O.Oracle(to_oracle(m), phi0, c0).step(100)
+    sim = L.Simulation(m, phi0, c0, precision=precision, mass_every=1)
+    sim.step(100)
+    phi, c, _ = sim.fields()
+    sim.close()
+    errs = dict(phi=rel_err(phi, o.phi), c=rel_err(c, o.c))
+    assert max(errs.values()) < tol, errs
