@@ -41,6 +41,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=20, help="steps of the FP64 comparison run")
+    ap.add_argument("--dev16-steps", type=int, default=50, help="timed steps of each 16-bit storage run (0 = skip)")
+    ap.add_argument("--e4-steps", type=int, default=10000,
+                    help="steps of the paper's 1024^2 porous experiment, timed in FP64 and FP32 (0 = skip)")
     ap.add_argument("--adj-steps", type=int, default=2000, help="steps of the 128^3 adjoint run (0 = skip)")
     ap.add_argument("--adj-every", type=int, default=100, help="checkpoint interval of the adjoint run")
     ap.add_argument("--batch-steps", type=int, default=40,
@@ -272,6 +275,39 @@ def adjoint_measurement(args, stream, hbm, fwd_bytes_per_node):
                     "reverse kernels = sweep - forward (the replay is the forward's kernels)"}
 
 
+PAPER_E4_V100_SECONDS = 70.0     # Sec. 5: 10^4 steps of the 1024^2 experiment on one V100
+
+
+def paper_e4_measurement(args, stream):
+    """The dissolution experiment of Sec. 5 (1024^2 D2Q9, W ~ 20 nodes,
+    lambda* = 230, anti-trapping, zero-flux walls) on a synthetic porous slice,
+    with and without the counter term: seconds for the paper's 10^4 steps in
+    FP64 and in FP32 (with the mass correction), CUDA events around the steps,
+    fields resident on the GPU.  The paper's code took 70 s on a V100 (context:
+    another GPU, another code, an unknown precision)."""
+    import torch
+    from paper_2111_05960_gb300 import lbpf as L
+    from paper_2111_05960_gb300 import workloads as WL
+    out = {"workload": "paper_e4_2d_1024_d2q9", "steps": args.e4_steps, "paper_v100_seconds": PAPER_E4_V100_SECONDS}
+    for prec in ("fp64", "fp32"):
+        for ct in (1, 0):
+            m, phi0, c0 = WL.paper_e4_2d(counter_term=ct)
+            sim = L.Simulation(m, phi0, c0, precision=prec, stream=stream.cuda_stream,
+                               mass_every=1 if prec == "fp32" else 0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.step(args.e4_steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            sec = e0.elapsed_time(e1) / 1e3
+            sim.close()
+            key = "%s_%s" % (prec, "counter_term" if ct else "no_counter_term")
+            out[key] = {"seconds": sec, "mlups": m.nodes * args.e4_steps / sec / 1e6,
+                        "speedup_vs_paper": PAPER_E4_V100_SECONDS * args.e4_steps / 1e4 / sec}
+    return out
+
+
 def cpu_model() -> str:
     """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
     try:
@@ -445,6 +481,36 @@ def run_ours(args):
                                  "fp32_speedup": ms64 / ms_per_step,
                                  "roofline": fp64_roofline(stream, N, ms64, wl.replace("_fp32", "_fp64"))}
 
+    # the 16-bit deviation-storage variants of the same step, for context
+    if prec == "fp32" and args.dev16_steps > 0:
+        dev = {}
+        for p16 in ("fp16dev", "bf16dev"):
+            s16 = L.Simulation(model, phi0, c0, precision=p16, stream=stream.cuda_stream, lattice=L.LBPF_D3Q19,
+                               mass_every=1)
+            s16.step(3)
+            torch.cuda.synchronize()
+            a16, b16 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a16.record(stream)
+            kp, kc, kr = s16.step_timed(args.dev16_steps)
+            b16.record(stream)
+            torch.cuda.synchronize()
+            ms16 = a16.elapsed_time(b16) / args.dev16_steps
+            m0, tgt = s16.solute_mass()
+            s16.close()
+            bp, bc = algorithmic_bytes(q, 4, 2)
+            dev[p16] = {"ms_per_step": ms16, "mlups": N / (ms16 * 1e-3) / 1e6,
+                        "step_frac": (bp + bc) * N / (ms16 * 1e-3) / 1e9 / hbm, "bytes_per_node": bp + bc,
+                        "kernel_ms": {"k_phi_step": kp / args.dev16_steps, "k_c_step": kc / args.dev16_steps},
+                        "mass_drift": (m0 - tgt) / tgt}
+        extra["dev16"] = dev
+
+    e4 = None
+    if args.e4_steps > 0 and prec == "fp32":
+        try:
+            e4 = paper_e4_measurement(args, stream)
+        except Exception as ex:   # reported, never silently dropped
+            e4 = {"error": str(ex)}
+
     batch = None
     if args.batch_steps > 0 and prec == "fp32":
         try:
@@ -511,7 +577,7 @@ def run_ours(args):
                           "parallelism": "replicas" if world > 1 else "single GPU",
                           "l2": "state %.1f GB per buffer set, larger than L2 (no flush needed)"
                                 % (N * (2 * q * store + 2 * real) / 1e9)},
-               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "batch_2d": batch, "adjoint": adj,
+               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "batch_2d": batch, "adjoint": adj, "paper_e4": e4,
                "gpu_launches": (4 if mass_every else 2) * args.steps, "clocks": clk,
                "mass": {"solute_before": m_before, "solute_after": m_after,
                         "relative_drift": (m_after - m_before) / m_before,

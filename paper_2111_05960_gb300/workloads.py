@@ -209,6 +209,32 @@ def slab_loss(phi, target):
     return loss, g[:, None, None].expand(phi.shape).contiguous()
 
 
+# ---- the paper's porous-medium experiment (Sec. 5) on a synthetic slice -----
+
+def paper_e4_2d(n=1024, counter_term=1, porosity=0.35, corr=16.0, seed=4):
+    """The dissolution experiment of Sec. 5 on a synthetic 2-D porous slice.
+
+    The paper's slice of a microtomography sample is not available; a Gaussian
+    random field thresholded at `porosity` (pores = liquid, correlation length
+    `corr` nodes, PCG64 `seed`) stands in for it.  Everything else follows
+    Sec. 5: the unit square on n x n nodes (dx = 1/n), dt = 5e-7, zero-flux
+    walls on all sides, M_phi = 1.2, W = 0.02, lambda* = 230, c_s^co = 0.6,
+    c_l^co = 0.5, mu_eq = 0.4, D_s = 0, D_l = 1, the anti-trapping current on
+    (a = 1/4), discontinuous start: phi = 0 and c = 0.6 in the solid, phi = 1
+    and c = 0.4 in the liquid.  Returned in lattice units (gamma = 1/M_phi, so
+    tau_g = tau_h = 3 M_phi dt/dx^2)."""
+    dx, dt = 1.0 / n, 5e-7
+    f = dt / (dx * dx)
+    tau = 3.0 * 1.2 * f
+    p = ModelParams(nx=n, ny=n, nz=1, bc=(1, 1, 0), tau_g=tau, tau_h=tau, W=0.02 / dx, lam=230.0,
+                    D_l=1.0 * f, D_s=0.0, c_s_co=0.6, c_l_co=0.5, mu_eq=0.4,
+                    counter_term=counter_term, anti_trapping=1, a_at=0.25)
+    pore = grf_mask((n, n), corr=corr, porosity=porosity, seed=seed)
+    phi = np.where(pore, 1.0, 0.0)[None, :, :]
+    c = np.where(pore, 0.4, 0.6)[None, :, :]
+    return p, phi, c
+
+
 # ---- batch of 2-D instances ------------------------------------------------
 
 @dataclass
