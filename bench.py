@@ -58,6 +58,25 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(value: float, world: int) -> float:
+    """The maximum of a per-rank time over all ranks (the job's time): an
+    all-reduce over the default process group (NCCL on GPUs, gloo on CPU)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(nodes_per_rank: int, steps: int, world: int, job_ms: float) -> float:
+    """Replicas: every rank advances its own copy of the workload, so the job's
+    throughput is all ranks' node updates over the slowest rank's time."""
+    return world * nodes_per_rank * steps / (job_ms * 1e-3) / 1e6
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -436,17 +455,13 @@ def run_ours(args):
     ev1.record(stream)
     barrier()
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world)
     m_c, m_phi = sim.mass()
     m_after, _ = sim.solute_mass()
     sim.close()
 
     ms_per_step = ms / args.steps
-    mlups = world * N * args.steps / (ms * 1e-3) / 1e6
+    mlups = whole_job_mlups(N, args.steps, world, ms)
     hbm, hbm_src = peaks()
     b_phi, b_c = algorithmic_bytes(q, real, store)
     avg_phi = k_phi_ms / args.steps
@@ -549,11 +564,8 @@ def run_ours(args):
         barrier()
         el = time.perf_counter() - t0
         s2.close()
-        if world > 1:
-            t = torch.tensor([el], device="cuda", dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            el = float(t.item())
-        e2e = {"value": world * N * args.steps / el / 1e6, "unit": "MLUPS",
+        el = max_over_ranks(el, world)
+        e2e = {"value": whole_job_mlups(N, args.steps, world, el * 1e3), "unit": "MLUPS",
                "h2d_bytes_per_step": 2 * N * 8 / args.steps,
                "d2h_bytes_per_step": (2 * N * 8) / args.steps + 16,
                "includes": "create from host fields, K x (step + FP64 mass read), final phi and c read"}
