@@ -95,10 +95,14 @@ struct AdjImpl {
         const AdjWork<R> T = work(ctx, a.work);
         const dim3 grid = adj_grid(ctx), block(kAdjBX, kAdjBY);
         const AdjCoef<R> C = make_adj_coef<R>(ctx->sp);
-        k_adj_h<L, R><<<grid, block, 0, ctx->stream>>>(
+        const StepParams& P = ctx->sp;
+        const bool walls = P.bc[0] || P.bc[1] || (L::D == 3 && P.bc[2]);
+        auto kh = walls ? k_adj_h<L, R, true> : k_adj_h<L, R, false>;
+        auto kg = walls ? k_adj_g<L, R, true> : k_adj_g<L, R, false>;
+        kh<<<grid, block, 0, ctx->stream>>>(
             ctx->sp, C, (const R*)s.h, (const R*)s.phi, (const R*)s.c, (const R*)phi1, (const R*)a.hb[cur],
             (const R*)a.cb[cur], (const R*)a.phib[cur], (R*)a.hb[nxt], T, a.blockacc, a.nblk);
-        k_adj_g<L, R><<<grid, block, 0, ctx->stream>>>(
+        kg<<<grid, block, 0, ctx->stream>>>(
             ctx->sp, C, (const R*)s.g, (const R*)s.phi, (const R*)s.c, (const R*)a.gb[cur], (R*)a.gb[nxt], T,
             (R*)a.phib[nxt], (R*)a.cb[nxt], a.blockacc, a.nblk);
         k_adj_finish<L, R><<<grid, block, 0, ctx->stream>>>(ctx->sp, T.grad, (R*)a.phib[nxt]);

@@ -335,7 +335,8 @@ __device__ __forceinline__ void adj_phi_sources(const AdjCoef<R>& C, const NodeF
 }
 
 // ---- composition part ---------------------------------------------------------
-template <class L, typename R>
+// WALLS = false: a fully periodic domain, where no link ever bounces back.
+template <class L, typename R, bool WALLS>
 __global__ void __launch_bounds__(kAdjThreads, adj_minb<R>())
 k_adj_h(const StepParams P, const AdjCoef<R> C, const R* __restrict__ h, const R* __restrict__ phi,
         const R* __restrict__ c, const R* __restrict__ phi1, const R* __restrict__ hb_in,
@@ -359,7 +360,7 @@ k_adj_h(const StepParams P, const AdjCoef<R> C, const R* __restrict__ h, const R
 #pragma unroll
         for (int k = 0; k < L::Q; ++k) {
             const long long d = i + nbr_off<L>(a, k);
-            const bool wall = (a.walls & out_bits<L>(k)) != 0;
+            const bool wall = WALLS && (a.walls & out_bits<L>(k)) != 0;
             const R s = wall ? hb_in[(long long)L::opp(k) * N + i] + cb_in[i] : hb_in[(long long)k * N + d] + cb_in[d];
             hb_out[(long long)k * N + i] = (R(1) - C.omh) * s;
             const R heq = k == 0 ? f.cc - R(1.0 - L::w(0)) * Q : R(L::w(k)) * Q;
@@ -391,7 +392,7 @@ k_adj_h(const StepParams P, const AdjCoef<R> C, const R* __restrict__ h, const R
 }
 
 // ---- phi part ---------------------------------------------------------------------
-template <class L, typename R>
+template <class L, typename R, bool WALLS>
 __global__ void __launch_bounds__(kAdjThreads, adj_minb_g<R>())
 k_adj_g(const StepParams P, const AdjCoef<R> C, const R* __restrict__ g, const R* __restrict__ phi,
         const R* __restrict__ c, const R* __restrict__ gb_in, R* __restrict__ gb_out, AdjWork<R> T,
@@ -418,7 +419,7 @@ k_adj_g(const StepParams P, const AdjCoef<R> C, const R* __restrict__ g, const R
 #pragma unroll
         for (int k = 0; k < L::Q; ++k) {
             const long long d = i + nbr_off<L>(a, k);
-            const bool wall = (a.walls & out_bits<L>(k)) != 0;
+            const bool wall = WALLS && (a.walls & out_bits<L>(k)) != 0;
             const R s = wall ? gb_in[(long long)L::opp(k) * N + i] + pt
                              : gb_in[(long long)k * N + d] + __ldg(T.pt + d);
             gb_out[(long long)k * N + i] = (R(1) - C.omg) * s;
