@@ -306,8 +306,13 @@ struct PhiSource {
         K = C.kct * pq;
         dw = -C.dw8M * (R(2) * pq * (R(1) - R(2) * f.ph));
     }
-    __device__ __forceinline__ R G(const AdjCoef<R>& C, const NodeFwd<L, R>& f, int k) const {
-        return R(L::w(k)) * (A + (C.counter_term ? K * edot3<L, R>(k, f.n) : dw));
+    // G_k with the switch resolved once per node, so the link loops carry no branch
+    __device__ __forceinline__ void per_link(const AdjCoef<R>& C, R& a0, R& kn) const {
+        a0 = A + (C.counter_term ? R(0) : dw);
+        kn = C.counter_term ? K : R(0);
+    }
+    __device__ __forceinline__ R G(int k, R a0, R kn, const NodeFwd<L, R>& f) const {
+        return R(L::w(k)) * (a0 + kn * edot3<L, R>(k, f.n));
     }
 };
 
@@ -414,6 +419,8 @@ k_adj_g(const StepParams P, const AdjCoef<R> C, const R* __restrict__ g, const R
         // link loop on memory latency).
         const R dphib_here = __ldg(T.dphi + i);
         const R pt = __ldg(T.pt + i);                    // adjoint of phi^{n+1} at this node
+        R ga0, gkn;
+        src.per_link(C, ga0, gkn);
         // s_k: adjoint of the post-collision population k; phi^{n+1} = sum g' + G/2
         R S0 = R(0), SV[3] = {R(0), R(0), R(0)}, Sneq = R(0);
 #pragma unroll
@@ -423,7 +430,7 @@ k_adj_g(const StepParams P, const AdjCoef<R> C, const R* __restrict__ g, const R
             const R s = wall ? gb_in[(long long)L::opp(k) * N + i] + pt
                              : gb_in[(long long)k * N + d] + __ldg(T.pt + d);
             gb_out[(long long)k * N + i] = (R(1) - C.omg) * s;
-            Sneq += s * (R(L::w(k)) * f.ph - R(0.5) * src.G(C, f, k) - g[(long long)k * N + i]);
+            Sneq += s * (R(L::w(k)) * f.ph - R(0.5) * src.G(k, ga0, gkn, f) - g[(long long)k * N + i]);
             S0 += R(L::w(k)) * s;
             add_we<L, R>(k, s, SV);
         }
