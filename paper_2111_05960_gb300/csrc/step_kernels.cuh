@@ -191,9 +191,21 @@ __device__ __forceinline__ R edot(int k, R vx, R vy, R vz) {
 template <typename R>
 __device__ __forceinline__ R rsqrt_reg(R g2, R eps2);
 template <>
-__device__ __forceinline__ double rsqrt_reg<double>(double g2, double eps2) { return 1.0 / sqrt(g2 + eps2); }
+__device__ __forceinline__ double rsqrt_reg<double>(double g2, double eps2) { return rsqrt(g2 + eps2); }
 template <>
-__device__ __forceinline__ float rsqrt_reg<float>(float g2, float eps2) { return 1.0f / sqrtf(g2 + eps2); }
+__device__ __forceinline__ float rsqrt_reg<float>(float g2, float eps2) { return rsqrtf(g2 + eps2); }
+
+// x / 36 for the weights w_k = m_k / 36.  FP32: correctly rounded, so the
+// rounding of each node's per-unit quantity is unbiased and the m_k-weighted
+// links conserve it (see lattice.cuh).  FP64: a multiplication by 1/36, whose
+// ~1e-17 relative bias is far below anything FP64 resolves, at a fraction of
+// the cost of a double division (the FP64 step is bound by the FP64 pipe).
+template <typename R>
+__device__ __forceinline__ R div36(R x);
+template <>
+__device__ __forceinline__ float div36<float>(float x) { return x / 36.0f; }
+template <>
+__device__ __forceinline__ double div36<double>(double x) { return x * (1.0 / 36.0); }
 
 // G^st + G^dw: the isotropic part of G_k / w_k (Eq. SourceG_ST, Eq. SourceG_dw;
 // S_phi of Eq. SourceTerm_Coexistence with p' = 6 phi (1 - phi);
@@ -373,7 +385,7 @@ __device__ __forceinline__ void phi_ingredients(const StepParams& P, const Coef<
         const R mu = closure_mu(C, ph, cst[s]);
         const R A = g_isotropic(C, ph, mu);
         V4<R> v;
-        v.a = (C.omg * ph + half_src * A) / R(36);      // per unit m_k (w_k = m_k / 36)
+        v.a = div36(C.omg * ph + half_src * A);         // per unit m_k (w_k = m_k / 36)
         if (P.counter_term) {
             R gx, gy, gz_;
             plane_gradient<L, BY, BX>(pm, p0, pp, c2, gx, gy, gz_);
@@ -410,7 +422,7 @@ __device__ __forceinline__ void c_ingredients(const StepParams& P, const Coef<R>
         const R inv = rsqrt_reg<R>(gx * gx + gy * gy + gz_ * gz_, C.eps2);
         const R f = mu * C.Dp + C.atk * dphi * inv;        // F = (mu D' + j_at / |grad|) grad
         V4<R> v;
-        v.a = p_term(C, ph, mu) / R(36);                 // P per unit m_k
+        v.a = div36(p_term(C, ph, mu));                  // P per unit m_k
         const R ff = C.kh36 * f;
         v.b = ff * gx; v.c = ff * gy; v.d = ff * gz_;
         ing[s] = v;
@@ -557,8 +569,8 @@ __device__ __forceinline__ void pull_combine(const KParams& K, const Coef<typena
         const R a = IS_PHI ? g.a : om * g.a;
         const R val = keep * f_old + mk * (a + sgn * edot<L>(k, g.b, g.c, g.d));
         v[k] = val;
-        if (IS_PHI) {
-            sum += val;
+        if (IS_PHI || sizeof(R) == 8) {
+            sum += val;          // FP64: a plain sum is unbiased far below FP64 resolution
         } else {
             const R t = sum + val;
             comp += (sum - t) + val;
@@ -581,7 +593,7 @@ __device__ __forceinline__ void pull_combine(const KParams& K, const Coef<typena
         moment_out[xi] = sum;                      // Eq. Moment0_LBM_Concent
         if (hold) {
             const R phin = phi_np1_in[xi];
-            const R Ps = p_term(C, phin, closure_mu(C, phin, sum)) / R(36);
+            const R Ps = div36(p_term(C, phin, closure_mu(C, phin, sum)));
             // the mass regulated by the correction is that of the populations as
             // stored (quantised), i.e. of the values the next step loads
             const R ref0 = sum - R(36 - L::m(0)) * Ps;
@@ -779,7 +791,7 @@ __global__ void k_init(const KParams K, const typename SP::real* __restrict__ ph
     const R mu = closure_mu(C, ph, cc);
     const R A = g_isotropic(C, ph, mu);
     const R kct = C.kct * ph * (R(1) - ph) * inv;
-    const R Ps = p_term(C, ph, mu) / R(36);
+    const R Ps = div36(p_term(C, ph, mu));
     const R f = mu * C.Dp;
     R hsum = R(0), hcomp = R(0);
 #pragma unroll
@@ -832,7 +844,7 @@ __global__ void k_pops_out(const KParams K, const typename SP::real* __restrict_
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= P.N) return;
     const R ph = phi[i], cc = c[i];
-    const R Ps = p_term(C, ph, closure_mu(C, ph, cc)) / R(36);
+    const R Ps = div36(p_term(C, ph, closure_mu(C, ph, cc)));
 #pragma unroll
     for (int k = 0; k < L::Q; ++k) {
         const R wk = R(L::w(k));
@@ -987,7 +999,7 @@ k_pop_mass(const KParams K, const typename SP::real* __restrict__ phi, const typ
     for (long long i = blockIdx.x * (long long)kMassThreads + threadIdx.x; i < P.N;
          i += (long long)gridDim.x * kMassThreads) {
         const R ph = phi[i], cc = c[i];
-        const R Ps = p_term(C, ph, closure_mu(C, ph, cc)) / R(36);
+        const R Ps = div36(p_term(C, ph, closure_mu(C, ph, cc)));
 #pragma unroll
         for (int k = 0; k < L::Q; ++k) {
             const R ref = (k == 0) ? cc - R(36 - L::m(0)) * Ps : R(L::m(k)) * Ps;
