@@ -130,3 +130,20 @@ def test_autotuner_times_every_shape_and_keeps_the_fastest():
     assert tile in L.BATCH_TILES
     assert np.all(ms > 0)
     assert ms[L.BATCH_TILES.index(tile)] == ms.min()
+
+
+def test_full_size_sweep_sampled_against_the_oracle():
+    """The 384-instance sweep the benchmark times (83 M nodes, FP32, the
+    autotuned tile, graphs): after 3 steps the smallest, the median and the
+    largest instance agree with the FP64 oracle run from the same fields."""
+    inst = WL.batch_2d(count=384, seed=1)
+    b = L.BatchSimulation([x.params for x in inst], [x.phi for x in inst], [x.c for x in inst], precision="fp32")
+    b.step(3)
+    sizes = np.array([x.params.nodes for x in inst])
+    order = np.argsort(sizes)
+    for i in (int(order[0]), int(order[len(order) // 2]), int(order[-1])):
+        phi, c, _ = b.fields(i)
+        o = O.Oracle(to_oracle(inst[i].params), inst[i].phi, inst[i].c).step(3)
+        errs = dict(phi=rel_err(phi, o.phi), c=rel_err(c, o.c))
+        assert max(errs.values()) < 2e-5, (i, inst[i].params.nx, errs)
+    b.close()

@@ -252,3 +252,30 @@ def test_reduced_precision_error_on_porous_medium(precision, tol):
     sim.close()
     errs = dict(phi=rel_err(phi, o.phi), c=rel_err(c, o.c))
     assert max(errs.values()) < tol, errs
+
+
+def test_disc_config_radius_over_20000_steps():
+    """The 512^2 disc at the equilibrium composition (R = 60, W = 3,
+    D_l = D_s = 0.05), 20000 steps, counter term on and off, FP64 and FP32
+    storage; radius R = sqrt(sum(1 - phi) / pi) every 2000 steps.  With the
+    counter term the disc stays put (drift < 0.1, the counter term cancels the
+    curvature motion); without it the disc shrinks monotonically.  FP32 follows
+    FP64 to 1e-3 in R.  (FP64 parity with the oracle on this disc: 100 steps,
+    test_disc_config_fp64_counter_term_on_and_off.)"""
+    radii = {}
+    for ct in (1, 0):
+        for prec in ("fp64", "fp32"):
+            m, phi0, c0 = WL.disc_2d(counter_term=ct, equilibrium=True)
+            sim = L.Simulation(m, phi0, c0, precision=prec, mass_every=0 if prec == "fp64" else 1)
+            r = [float(np.sqrt((1.0 - phi0).sum() / np.pi))]
+            for _ in range(10):
+                sim.step(2000)
+                phi, _, _ = sim.fields()
+                r.append(float(np.sqrt((1.0 - phi).sum() / np.pi)))
+            sim.close()
+            radii[(ct, prec)] = np.array(r)
+    r_on, r_off = radii[(1, "fp64")], radii[(0, "fp64")]
+    assert np.max(np.abs(r_on - r_on[0])) < 0.1, r_on
+    assert np.all(np.diff(r_off) < 0) and r_off[-1] < r_off[0] - 1.0, r_off
+    for ct in (1, 0):
+        assert np.max(np.abs(radii[(ct, "fp32")] - radii[(ct, "fp64")])) < 1e-3, ct
