@@ -31,12 +31,19 @@ struct BatchInst {
 struct BatchTile {
     int bx, rows;
 };
-// Candidate tile shapes (BX threads per block, 1024 / BX resident blocks).
+// Candidate tile shapes (BX threads per block, LBPF_BATCH_TPSM / BX resident
+// blocks).  The instance parameters are read from shared memory, so the
+// compiler keeps the link offsets and coefficients in registers: at 1024
+// threads per SM (64 registers) the kernels spill, at 768 (80 registers) they
+// do not; 768 is also the fastest of 512-1024 on the 384-instance sweep.
 constexpr BatchTile kBatchTiles[] = {{64, 16}, {64, 32}, {128, 16}, {128, 32}, {256, 16}};
 constexpr int kNumBatchTiles = sizeof(kBatchTiles) / sizeof(kBatchTiles[0]);
+#ifndef LBPF_BATCH_TPSM
+#define LBPF_BATCH_TPSM 768
+#endif
 
 template <class SP, bool IS_PHI, int BX, int ROWS>
-__global__ void __launch_bounds__(BX, 1024 / BX)
+__global__ void __launch_bounds__(BX, LBPF_BATCH_TPSM / BX)
 k_batch_step(const BatchInst* __restrict__ inst, const int* __restrict__ tile_inst, int ntiles,
              const typename SP::store_t* __restrict__ fin, typename SP::store_t* __restrict__ fout,
              const typename SP::real* __restrict__ phi_n, const typename SP::real* __restrict__ phi_np1,

@@ -48,8 +48,12 @@ def _compare(m, phi0, c0, steps, precision="fp64", pops=True):
     return errs
 
 
-# 2-D shapes span several 32x8 tiles with ragged tails, plus degenerate 1-wide axes
+# 2-D shapes: rows marched in 128-node segments, 16 rows per block; several
+# segments and row chunks with ragged tails (odd chunk lengths exercise the
+# one-row load lookahead), plus degenerate 1-wide axes
 @pytest.mark.parametrize("shape,bc,ct,at", [
+    ((1, 37, 300), (1, 1, 0), 1, 1),
+    ((1, 50, 259), (0, 0, 0), 0, 1),
     ((1, 21, 70), (0, 0, 0), 1, 1),
     ((1, 21, 70), (1, 0, 0), 0, 1),
     ((1, 17, 33), (1, 1, 0), 1, 0),
