@@ -187,16 +187,21 @@ lbpf_status lbpf_lattice_info(int32_t lattice, int32_t *q, int32_t *e, double *w
 
 /* Batch of 2-D instances of uneven size in one context (a parameter sweep,
  * counter term on and off, ...), stepped together: each kernel phase is one
- * persistent launch over a flat list of 32 x 8 tiles of all instances, so the
- * work is balanced whatever the size mix.  p[i], phi0[i], c0[i] describe
- * instance i exactly as for lbpf_create (each with its own sizes, walls and
- * parameters); all instances must be D2Q9 with the same precision and
- * mass_every = 0.  The fields are copied; ptr_is_device says where phi0[i] and
- * c0[i] live.  lbpf_step, lbpf_step_timed and lbpf_mass (sums over all
- * instances) work on a batch; lbpf_get_fields, lbpf_get_populations and
- * lbpf_solute_mass return LBPF_EUNSUPPORTED (use the calls below).
- * Errors: EINVAL (NULL pointers, n < 1, an invalid instance: the message names
- * it), EUNSUPPORTED (non-D2Q9 instance, mass_every != 0), ENOMEM, ECUDA. */
+ * persistent launch over a flat list of row-marched tiles (BX columns x ROWS
+ * rows, the shape picked by an autotuner at creation, see lbpf_batch_tile) of
+ * all instances, so the work is balanced whatever the size mix.  p[i], phi0[i],
+ * c0[i] describe instance i exactly as for lbpf_create (each with its own
+ * sizes, walls and parameters); all instances must be D2Q9 with the same
+ * precision, mass_every = 0, checkpoint_every = 0 and 9 nx ny x (bytes per
+ * stored value: 8 FP64, 4 FP32, 2 for 16-bit storage) < 2^31 (the kernels
+ * address within an instance with 32-bit byte offsets).  The fields are copied;
+ * ptr_is_device says where phi0[i] and c0[i] live.  lbpf_step,
+ * lbpf_step_timed and lbpf_mass (sums over all instances) work on a batch;
+ * lbpf_get_fields, lbpf_get_populations and lbpf_solute_mass return
+ * LBPF_EUNSUPPORTED (use the calls below).
+ * Errors: EINVAL (NULL pointers, n < 1, an invalid or oversized instance: the
+ * message names it), EUNSUPPORTED (non-D2Q9 instance, mass_every != 0,
+ * checkpoint_every != 0), ENOMEM, ECUDA. */
 lbpf_status lbpf_create_batch(const lbpf_params *p, int32_t n, const double *const *phi0,
                               const double *const *c0, int32_t ptr_is_device, void *cuda_stream,
                               lbpf_ctx **out);

@@ -209,6 +209,10 @@ lbpf_status lbpf_create_batch(const lbpf_params* p, int32_t n, const double* con
         if (!phi0[i] || !c0[i]) return fail(nullptr, LBPF_EINVAL, "NULL field pointer of instance " + std::to_string(i));
         if (validate(&p[i], why) != LBPF_OK) return fail(nullptr, LBPF_EINVAL, "instance " + std::to_string(i) + ": " + why);
         if (p[i].lattice != LBPF_D2Q9) return fail(nullptr, LBPF_EUNSUPPORTED, "batches hold 2-D D2Q9 instances");
+        const long long sb = p[i].precision == LBPF_FP64 ? 8 : (p[i].precision == LBPF_FP32 ? 4 : 2);
+        if (9LL * p[i].nx * p[i].ny * sb >= (1LL << 31))
+            return fail(nullptr, LBPF_EINVAL,
+                        "instance " + std::to_string(i) + ": 9 nx ny x bytes per value must stay below 2^31");
         if (p[i].precision != p[0].precision) return fail(nullptr, LBPF_EINVAL, "all instances need one precision");
         if (p[i].mass_every != 0) return fail(nullptr, LBPF_EUNSUPPORTED, "mass correction is not built for batches");
         if (p[i].checkpoint_every != 0) return fail(nullptr, LBPF_EUNSUPPORTED, "the adjoint is not built for batches");

@@ -297,6 +297,8 @@ KParams lbpf_rt::make_kparams(const lbpf_params* p) {
     kp.cd = make_coef<double>(kp.P);
     kp.cf = make_coef<float>(kp.P);
     const int q = p->lattice == LBPF_D3Q19 ? 19 : 9;
+    const long long sb = p->precision == LBPF_FP64 ? 8 : (p->precision == LBPF_FP32 ? 4 : 2);
+    const bool fits = (long long)q * kp.P.N * sb < (1LL << 31);
     for (int k = 0; k < 19; ++k) {
         int e[3] = {0, 0, 0};
         if (k < q) {
@@ -304,8 +306,10 @@ KParams lbpf_rt::make_kparams(const lbpf_params* p) {
             else { e[0] = D2Q9::ex(k); e[1] = D2Q9::ey(k); }
         }
         const long long nx = p->nx, nxy = (long long)p->nx * p->ny;
-        kp.kN[k] = (long long)k * kp.P.N;
-        kp.koff[k] = kp.kN[k] - (e[0] + e[1] * nx + e[2] * nxy);
+        kp.kNB[k] = (long long)k * kp.P.N * sb;
+        kp.koffB[k] = kp.kNB[k] - (e[0] + e[1] * nx + e[2] * nxy) * sb;
+        kp.kNB32[k] = fits ? (int)kp.kNB[k] : 0;
+        kp.koffB32[k] = fits ? (int)kp.koffB[k] : 0;
     }
     return kp;
 }

@@ -34,6 +34,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "lattice.cuh"
 
 namespace lbpf {
@@ -87,11 +89,39 @@ struct KParams {
     StepParams P;
     Coef<double> cd;
     Coef<float> cf;
-    // per link k: k N - (ex + ey nx + ez nx ny), the element offset of the upstream
-    // population from x for a node whose neighbours are all inside (no wrap), and k N
-    long long koff[19];
-    long long kN[19];
+    // per link k, in BYTES of the stored populations (element offset x bytes
+    // per stored value, so that an address is one add): k N - (ex + ey nx +
+    // ez nx ny), the offset of the upstream population from x for a node whose
+    // neighbours are all inside (no wrap), and k N
+    long long koffB[19];
+    long long kNB[19];
+    // the same as 32-bit values when they fit (else 0): the batch kernels,
+    // whose instances are bounded in size, index with them
+    int koffB32[19];
+    int kNB32[19];
 };
+
+// Byte offsets of the links in the index type of a march (64-bit, or 32-bit
+// for batch instances).
+template <typename I>
+__device__ __forceinline__ I link_src(const KParams& K, int k);
+template <>
+__device__ __forceinline__ long long link_src<long long>(const KParams& K, int k) { return K.koffB[k]; }
+template <>
+__device__ __forceinline__ int link_src<int>(const KParams& K, int k) { return K.koffB32[k]; }
+template <typename I>
+__device__ __forceinline__ I link_base(const KParams& K, int k);
+template <>
+__device__ __forceinline__ long long link_base<long long>(const KParams& K, int k) { return K.kNB[k]; }
+template <>
+__device__ __forceinline__ int link_base<int>(const KParams& K, int k) { return K.kNB32[k]; }
+
+// p advanced by a byte offset
+template <typename T, typename I>
+__device__ __forceinline__ T* byte_add(T* p, I off) {
+    using C = typename std::conditional<std::is_const<T>::value, const char, char>::type;
+    return reinterpret_cast<T*>(reinterpret_cast<C*>(p) + off);
+}
 
 template <typename R>
 __device__ __forceinline__ const Coef<R>& coef(const KParams& K);
@@ -434,7 +464,7 @@ __device__ __forceinline__ void c_ingredients(const StepParams& P, const Coef<R>
 //
 // Upstream node of link k: (x - ex, y - ey, z - ez), wrapped on periodic axes;
 // beyond a wall the link bounces back to the node itself.  `fast`: every
-// upstream node is inside, so the source is xi + koff[k] (one add).  Otherwise
+// upstream node is inside, so the source is the node address + koffB[k] (one add).  Otherwise
 // the wrapped x index, row and plane offsets for e = -1, 0, 1 are computed once
 // and a link's source costs two adds and no branch.
 // Exact solute mass of the populations a thread has written, as an unevaluated
@@ -450,35 +480,35 @@ struct MassAcc {
     }
 };
 
-template <class L, class SP, bool IS_PHI, bool WALLS>
+template <class L, class SP, bool IS_PHI, bool WALLS, typename I = long long>
 struct PullState {
     using R = typename SP::real;
     R old[L::Q];
     R cx;
     unsigned wallmask;
-    long long xi;
+    I xi;
 };
 
-template <class L, class SP, bool IS_PHI, bool WALLS>
+template <class L, class SP, bool IS_PHI, bool WALLS, typename I>
 __device__ __forceinline__ void pull_load(const KParams& K, const typename SP::store_t* __restrict__ fin,
                                           const typename SP::real* __restrict__ c_n, int x, int y, int z, bool fast,
-                                          PullState<L, SP, IS_PHI, WALLS>& st) {
+                                          PullState<L, SP, IS_PHI, WALLS, I>& st) {
     using R = typename SP::real;
     const StepParams& P = K.P;
-    const long long nxy = (long long)P.nx * P.ny;
-    const long long xi = (long long)z * nxy + (long long)y * P.nx + x;
+    const I nxy = (I)P.nx * P.ny;
+    const I xi = (I)z * nxy + (I)y * P.nx + x;
     st.xi = xi;
     st.wallmask = 0u;
     st.cx = IS_PHI ? R(0) : c_n[xi];
     if (fast) {
         const typename SP::store_t* base = fin + xi;
 #pragma unroll
-        for (int k = 0; k < L::Q; ++k) st.old[k] = SP::load(base, K.koff[k], R(0));
+        for (int k = 0; k < L::Q; ++k) st.old[k] = SP::load(byte_add(base, link_src<I>(K, k)), 0, R(0));
         return;
     }
     // source offsets indexed by e + 1: e = +1 reads the node at -1, e = -1 the node at +1
     int SX[3], SY[3];
-    long long SZ[3];
+    I SZ[3];
     bool WX[3], WY[3], WZ[3];
     {
         const bool lo = x == 0, hi = x == P.nx - 1;
@@ -495,18 +525,19 @@ __device__ __forceinline__ void pull_load(const KParams& K, const typename SP::s
     if (L::D == 3) {
         const bool lo = z == 0, hi = z == P.nz - 1;
         SZ[1] = z * nxy; WZ[1] = false;
-        SZ[2] = (long long)(lo ? (WALLS && P.bc[2] ? z : P.nz - 1) : z - 1) * nxy; WZ[2] = WALLS && lo && P.bc[2];
-        SZ[0] = (long long)(hi ? (WALLS && P.bc[2] ? z : 0) : z + 1) * nxy;        WZ[0] = WALLS && hi && P.bc[2];
+        SZ[2] = (I)(lo ? (WALLS && P.bc[2] ? z : P.nz - 1) : z - 1) * nxy; WZ[2] = WALLS && lo && P.bc[2];
+        SZ[0] = (I)(hi ? (WALLS && P.bc[2] ? z : 0) : z + 1) * nxy;        WZ[0] = WALLS && hi && P.bc[2];
     } else {
         SZ[0] = SZ[1] = SZ[2] = 0; WZ[0] = WZ[1] = WZ[2] = false;
     }
 #pragma unroll
     for (int k = 0; k < L::Q; ++k) {
         const bool wall = WALLS && (WX[L::ex(k) + 1] || WY[L::ey(k) + 1] || WZ[L::ez(k) + 1]);
-        const long long si = SZ[L::ez(k) + 1] + SY[L::ey(k) + 1] + SX[L::ex(k) + 1];
+        const I si = SZ[L::ez(k) + 1] + SY[L::ey(k) + 1] + SX[L::ex(k) + 1];
         // half-way bounce-back: f_k(x, n+1) = f*_{opp k}(x, n)
-        const long long addr = wall ? K.kN[L::opp(k)] + xi : K.kN[k] + si;
-        st.old[k] = SP::load(fin, addr, R(0));
+        const typename SP::store_t* src = wall ? byte_add(fin + xi, link_base<I>(K, L::opp(k)))
+                                               : byte_add(fin + si, link_base<I>(K, k));
+        st.old[k] = SP::load(src, 0, R(0));
         st.wallmask |= (wall ? 1u : 0u) << k;
     }
 }
@@ -514,7 +545,7 @@ __device__ __forceinline__ void pull_load(const KParams& K, const typename SP::s
 // Collision of each pulled population at its upstream node from the ingredient
 // planes im (z-1), i0 (z), ip (z+1) (phi planes fm, f0, fp likewise), the new
 // moment, and the stores.
-template <class L, class SP, int BY, int BX, bool IS_PHI, bool WALLS>
+template <class L, class SP, int BY, int BX, bool IS_PHI, bool WALLS, typename I>
 __device__ __forceinline__ void pull_combine(const KParams& K, const Coef<typename SP::real>& C,
                                              typename SP::store_t* __restrict__ fout,
                                              const V4<typename SP::real>* im, const V4<typename SP::real>* i0,
@@ -523,11 +554,11 @@ __device__ __forceinline__ void pull_combine(const KParams& K, const Coef<typena
                                              const typename SP::real* sA,
                                              const typename SP::real* __restrict__ phi_np1_in,
                                              typename SP::real* __restrict__ moment_out,
-                                             const PullState<L, SP, IS_PHI, WALLS>& st,
+                                             const PullState<L, SP, IS_PHI, WALLS, I>& st,
                                              MassAcc<typename SP::real>& macc) {
     using R = typename SP::real;
     using G = Geo<L, BY, BX>;
-    const long long xi = st.xi;
+    const I xi = st.xi;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int c1 = (ty + G::OY1) * G::X1 + (tx + 1);
     const int c2 = (ty + G::OY2) * G::X2 + (tx + 2);
@@ -550,7 +581,7 @@ __device__ __forceinline__ void pull_combine(const KParams& K, const Coef<typena
         const R heq0 = st.cx - R(36 - L::m(0)) * i0[c1].a;   // h^eq_0 = c - (1 - w_0) P
         v[0] = keep * (SP::deviation ? st.old[0] + heq0 : st.old[0]) + om * heq0;
         sum = v[0];
-        if (!hold) SP::store(out, K.kN[0], v[0], R(0));
+        if (!hold) SP::store(byte_add(out, link_base<I>(K, 0)), 0, v[0], R(0));
     }
 #pragma unroll
     for (int k = k0; k < L::Q; ++k) {
@@ -576,7 +607,7 @@ __device__ __forceinline__ void pull_combine(const KParams& K, const Coef<typena
             comp += (sum - t) + val;
             sum = t;
         }
-        if (!hold) SP::store(out, K.kN[k], val, R(0));
+        if (!hold) SP::store(byte_add(out, link_base<I>(K, k)), 0, val, R(0));
     }
     if (!IS_PHI) {
         if (!hold) macc.add(sum, comp);   // the node's exact population mass is sum + comp
@@ -587,7 +618,7 @@ __device__ __forceinline__ void pull_combine(const KParams& K, const Coef<typena
         moment_out[xi] = phin;
         if (hold) {
 #pragma unroll
-            for (int k = 0; k < L::Q; ++k) SP::store(out, K.kN[k], v[k], R(L::w(k)) * phin);
+            for (int k = 0; k < L::Q; ++k) SP::store(byte_add(out, link_base<I>(K, k)), 0, v[k], R(L::w(k)) * phin);
         }
     } else {
         moment_out[xi] = sum;                      // Eq. Moment0_LBM_Concent
@@ -597,12 +628,12 @@ __device__ __forceinline__ void pull_combine(const KParams& K, const Coef<typena
             // the mass regulated by the correction is that of the populations as
             // stored (quantised), i.e. of the values the next step loads
             const R ref0 = sum - R(36 - L::m(0)) * Ps;
-            SP::store(out, K.kN[0], v[0], ref0);
+            SP::store(byte_add(out, link_base<I>(K, 0)), 0, v[0], ref0);
             R ms = SP::stored(v[0], ref0), mcomp = R(0);
 #pragma unroll
             for (int k = 1; k < L::Q; ++k) {
                 const R ref = R(L::m(k)) * Ps;
-                SP::store(out, K.kN[k], v[k], ref);
+                SP::store(byte_add(out, link_base<I>(K, k)), 0, v[k], ref);
                 const R vs = SP::stored(v[k], ref);
                 const R t = ms + vs;
                 mcomp += (ms - t) + vs;
@@ -633,7 +664,7 @@ __device__ __forceinline__ void block_mass_out(const MassAcc<R>& m, double* __re
 // One z-marching pass of either kernel.  The composition kernel also sums the
 // exact mass of the populations it writes into mass_partials (one FP64 value
 // per block) when that pointer is not null.
-template <class L, class SP, int BY, int ZCH, bool IS_PHI, bool WALLS, int BX = 32>
+template <class L, class SP, int BY, int ZCH, bool IS_PHI, bool WALLS, int BX = 32, typename I = long long>
 __device__ __forceinline__ void march(const KParams& K, const typename SP::store_t* __restrict__ fin,
                                       typename SP::store_t* __restrict__ fout,
                                       const typename SP::real* __restrict__ phi_n,
@@ -657,7 +688,7 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
     const bool active_xy = x < P.nx && y < P.ny;
     const bool inside2 = x0 >= 2 && x0 + G::BX + 2 <= P.nx && y0 >= G::OY2 && y0 + BY + G::OY2 <= P.ny;
     const bool inside1 = x0 >= 1 && x0 + G::BX + 1 <= P.nx && y0 >= G::OY1 && y0 + BY + G::OY1 <= P.ny;
-    PullState<L, SP, IS_PHI, WALLS> st;
+    PullState<L, SP, IS_PHI, WALLS, I> st;
     MassAcc<R> macc{R(0), R(0)};
 
     // the ring inputs of plane zg go to stage buffer zg & 1
@@ -711,11 +742,11 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
             fetch_ring(z + 2);
         }
         cp_async_commit();
-        if (active_xy) pull_load<L, SP, IS_PHI, WALLS>(K, fin, c_n, x, y, z, inside1 && z >= 1 && z + 1 < P.nz, st);
+        if (active_xy) pull_load<L, SP, IS_PHI, WALLS, I>(K, fin, c_n, x, y, z, inside1 && z >= 1 && z + 1 < P.nz, st);
         ingredients(islot(z + 1), fslot(z), fslot(z + 1), fslot(z + 2), z + 1);
         __syncthreads();
         if (active_xy)
-            pull_combine<L, SP, BY, BX, IS_PHI, WALLS>(K, C, fout, sing + islot(z - 1) * G::P1,
+            pull_combine<L, SP, BY, BX, IS_PHI, WALLS, I>(K, C, fout, sing + islot(z - 1) * G::P1,
                                                    sing + islot(z) * G::P1, sing + islot(z + 1) * G::P1,
                                                    fslot(z - 1), fslot(z), fslot(z + 1), sA + islot(z) * G::P1,
                                                    phi_np1, moment_out, st, macc);
