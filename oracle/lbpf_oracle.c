@@ -36,6 +36,17 @@
  *        h*_k = h_k - (h_k - (h^eq_k - H_k/2)) / (tau_h + 1/2) + H_k
  *   9. streaming of h as for g, c' = sum_k h_k (Eq. Moment0_LBM_Concent)
  *
+ * Two variants of the composition scheme, both named in Sec. 3.3:
+ *   - h_eq_alt = 1: the alternative equilibrium of Eq. Seq_Concent_Alt with
+ *     H_k = 0 (Eq. LBE_Concent_Alt): h^eq,alt_k = w_k [gamma D mu + e_k.F / xi_s^2]
+ *     for k != 0 (xi_s^2 = 1/3 in lattice units), h^eq,alt_0 = h^eq_0, and
+ *     h*_k = h_k - (h_k - h^eq,alt_k) / (tau_h + 1/2).  Without H there is no
+ *     shifted variable: the populations start at h_k = h^eq,alt_k (dphi/dt = 0).
+ *   - h_lattice = 1: h on the smaller lattice of the paper's code (Sec. 3.1),
+ *     D2Q5 in 2-D and D3Q7 in 3-D, with weights chosen so that xi_s^2 = 1/3 as
+ *     for D2Q9 (tau_h = 3 dt / (gamma dx^2) unchanged): D2Q5 w = 1/3, 1/6;
+ *     D3Q7 w = 0, 1/6.  g, the gradient and the normal keep D2Q9 / D3Q19.
+ *
  * Lattices: D2Q9 in the paper's ordering (Sec. 3.1); D3Q19 for the 3-D
  * workloads (the paper names D3Q19 among the lattices of its code, Sec. 3.1),
  * with the same directional-derivative gradient over its 18 links.
@@ -67,6 +78,8 @@ typedef struct {
     int anti_trapping;      /* 1: j_at included */
     double a_at;            /* coefficient a of j_at */
     double eps_n;           /* regularisation of |grad phi| in n */
+    int h_lattice;          /* 0: h on the g lattice; 1: D2Q5 / D3Q7 */
+    int h_eq_alt;           /* 1: h^eq,alt with H = 0 (Eq. Seq_Concent_Alt) */
 } or_params;
 
 /* ---- lattices ---------------------------------------------------------- */
@@ -94,6 +107,12 @@ static const double D3Q19_W[19] = {
     1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0,
     1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
 
+/* D2Q5 (the first five D2Q9 directions) and D3Q7 (rest and the six face
+ * links, opposites next to each other), for h only; weights with
+ * xi_s^2 = sum_k w_k e_kx^2 = 1/3. */
+static const double D2Q5_W[5] = {1.0 / 3.0, 1.0 / 6.0, 1.0 / 6.0, 1.0 / 6.0, 1.0 / 6.0};
+static const double D3Q7_W[7] = {0.0, 1.0 / 6.0, 1.0 / 6.0, 1.0 / 6.0, 1.0 / 6.0, 1.0 / 6.0, 1.0 / 6.0};
+
 typedef struct {
     int q;
     const int (*e)[3];
@@ -101,11 +120,10 @@ typedef struct {
     int opp[19];
 } lattice;
 
-static lattice get_lattice(int dim)
+static lattice make_lattice(int q, const int (*e)[3], const double *w)
 {
     lattice L;
-    if (dim == 3) { L.q = 19; L.e = D3Q19_E; L.w = D3Q19_W; }
-    else          { L.q = 9;  L.e = D2Q9_E;  L.w = D2Q9_W; }
+    L.q = q; L.e = e; L.w = w;
     for (int k = 0; k < L.q; ++k)
         for (int j = 0; j < L.q; ++j)
             if (L.e[j][0] == -L.e[k][0] && L.e[j][1] == -L.e[k][1] && L.e[j][2] == -L.e[k][2])
@@ -113,11 +131,27 @@ static lattice get_lattice(int dim)
     return L;
 }
 
-/* Lattice tables, exported so that the tests can check the identities the
- * scheme relies on (sum w = 1, sum w e = 0, 3 sum w e e = I). */
-int or_lattice(int dim, int *e_out /* q*3 */, double *w_out /* q */, int *opp_out /* q */)
+static lattice get_lattice(int dim)
 {
-    lattice L = get_lattice(dim);
+    return dim == 3 ? make_lattice(19, D3Q19_E, D3Q19_W) : make_lattice(9, D2Q9_E, D2Q9_W);
+}
+
+/* The lattice of the composition populations h. */
+static lattice get_h_lattice(const or_params *p)
+{
+    if (!p->h_lattice) return get_lattice(p->dim);
+    return p->dim == 3 ? make_lattice(7, D3Q19_E, D3Q7_W) : make_lattice(5, D2Q9_E, D2Q5_W);
+}
+
+/* Lattice tables, exported so that the tests can check the identities the
+ * scheme relies on (sum w = 1, sum w e = 0, 3 sum w e e = I).  code: 2 D2Q9,
+ * 3 D3Q19, 5 D2Q5, 7 D3Q7. */
+int or_lattice(int code, int *e_out /* q*3 */, double *w_out /* q */, int *opp_out /* q */)
+{
+    lattice L;
+    if (code == 5) L = make_lattice(5, D2Q9_E, D2Q5_W);
+    else if (code == 7) L = make_lattice(7, D3Q19_E, D3Q7_W);
+    else L = get_lattice(code);
     for (int k = 0; k < L.q; ++k) {
         for (int a = 0; a < 3; ++a) e_out[3 * k + a] = L.e[k][a];
         w_out[k] = L.w[k];
@@ -227,6 +261,17 @@ static double h_equilibrium(const or_params *p, const lattice *L, int k,
     return L->w[k] * gamma * D * mu;
 }
 
+/* h^eq,alt of Eq. Seq_Concent_Alt: the flux enters the equilibrium through its
+ * first moment, e_k.F / xi_s^2 with xi_s^2 = 1/3, and H_k = 0. */
+static double h_equilibrium_alt(const or_params *p, const lattice *L, int k,
+                                double phi, double c, double mu, const double F[3])
+{
+    double heq = h_equilibrium(p, L, k, phi, c, mu);
+    if (k == 0) return heq;
+    double eF = L->e[k][0] * F[0] + L->e[k][1] * F[1] + L->e[k][2] * F[2];
+    return heq + L->w[k] * eF / (1.0 / 3.0);
+}
+
 /* Gradient by directional derivatives (Eq. DerivDirec_Grad and Eq. Grad). */
 static void gradient_at(const or_params *p, const lattice *L, const double *phi,
                         int x, int y, int z, double grad[3])
@@ -287,6 +332,7 @@ int or_init(const or_params *p, const double *phi0, const double *c0,
             double *g, double *h, double *phi, double *c)
 {
     lattice L = get_lattice(p->dim);
+    lattice LH = get_h_lattice(p);
     long N = (long)p->nx * p->ny * p->nz;
     memcpy(phi, phi0, sizeof(double) * N);
     memcpy(c, c0, sizeof(double) * N);
@@ -304,8 +350,14 @@ int or_init(const or_params *p, const double *phi0, const double *c0,
             for (int k = 0; k < L.q; ++k) {
                 double Gk = source_G(p, &L, k, phi[i], mu, nvec);
                 g[k * N + i] = L.w[k] * phi[i] - 0.5 * Gk;
-                double Hk = source_H(p, &L, k, F);
-                h[k * N + i] = h_equilibrium(p, &L, k, phi[i], c[i], mu) - 0.5 * Hk;
+            }
+            for (int k = 0; k < LH.q; ++k) {
+                if (p->h_eq_alt) {
+                    h[k * N + i] = h_equilibrium_alt(p, &LH, k, phi[i], c[i], mu, F);
+                } else {
+                    double Hk = source_H(p, &LH, k, F);
+                    h[k * N + i] = h_equilibrium(p, &LH, k, phi[i], c[i], mu) - 0.5 * Hk;
+                }
             }
         }
     }
@@ -314,7 +366,7 @@ int or_init(const or_params *p, const double *phi0, const double *c0,
 
 /* ---- one time step ----------------------------------------------------- */
 
-static int step_once(const or_params *p, const lattice *L, double *g, double *h,
+static int step_once(const or_params *p, const lattice *L, const lattice *LH, double *g, double *h,
                      double *phi, double *c, double *gs, double *hs,
                      double *mu, double *grad, double *nvec, double *Gsum, double *phinew)
 {
@@ -368,10 +420,15 @@ static int step_once(const or_params *p, const lattice *L, double *g, double *h,
             double dphi = phinew[i] - phi[i];
             double F[3];
             flux_F(p, mu[i], dphi, grad + 3 * i, nvec + 3 * i, F);
-            for (int k = 0; k < q; ++k) {
-                double Hk = source_H(p, L, k, F);
-                double heq_tilde = h_equilibrium(p, L, k, phi[i], c[i], mu[i]) - 0.5 * Hk;
-                hs[k * N + i] = h[k * N + i] - omh * (h[k * N + i] - heq_tilde) + Hk;
+            for (int k = 0; k < LH->q; ++k) {
+                if (p->h_eq_alt) {
+                    double heq = h_equilibrium_alt(p, LH, k, phi[i], c[i], mu[i], F);
+                    hs[k * N + i] = h[k * N + i] - omh * (h[k * N + i] - heq);
+                } else {
+                    double Hk = source_H(p, LH, k, F);
+                    double heq_tilde = h_equilibrium(p, LH, k, phi[i], c[i], mu[i]) - 0.5 * Hk;
+                    hs[k * N + i] = h[k * N + i] - omh * (h[k * N + i] - heq_tilde) + Hk;
+                }
             }
         }
     }
@@ -382,9 +439,9 @@ static int step_once(const or_params *p, const lattice *L, double *g, double *h,
         for (int x = 0; x < p->nx; ++x) {
             long i = idx(p, x, y, z);
             double s = 0.0;
-            for (int k = 0; k < q; ++k) {
-                long src = upstream_index(p, L, k, x, y, z);
-                double v = (src < 0) ? hs[L->opp[k] * N + i] : hs[k * N + src];
+            for (int k = 0; k < LH->q; ++k) {
+                long src = upstream_index(p, LH, k, x, y, z);
+                double v = (src < 0) ? hs[LH->opp[k] * N + i] : hs[k * N + src];
                 h[k * N + i] = v;
                 s += v;
             }
@@ -395,10 +452,12 @@ static int step_once(const or_params *p, const lattice *L, double *g, double *h,
     return 0;
 }
 
-/* Advance nsteps.  Returns 0, or -1 on allocation failure. */
+/* Advance nsteps.  h holds q_h planes (9 / 19, or 5 / 7 with h_lattice = 1).
+ * Returns 0, or -1 on allocation failure. */
 int or_step(const or_params *p, double *g, double *h, double *phi, double *c, int nsteps)
 {
     lattice L = get_lattice(p->dim);
+    lattice LH = get_h_lattice(p);
     long N = (long)p->nx * p->ny * p->nz;
     int q = L.q;
     double *gs = malloc(sizeof(double) * q * N);
@@ -411,7 +470,7 @@ int or_step(const or_params *p, double *g, double *h, double *phi, double *c, in
     int rc = 0;
     if (!gs || !hs || !mu || !grad || !nvec || !Gsum || !phinew) rc = -1;
     for (int s = 0; rc == 0 && s < nsteps; ++s)
-        rc = step_once(p, &L, g, h, phi, c, gs, hs, mu, grad, nvec, Gsum, phinew);
+        rc = step_once(p, &L, &LH, g, h, phi, c, gs, hs, mu, grad, nvec, Gsum, phinew);
     free(gs); free(hs); free(mu); free(grad); free(nvec); free(Gsum); free(phinew);
     return rc;
 }
@@ -562,6 +621,7 @@ static void finish_adjoint(const or_params *p, const lattice *L, const double *g
 int or_step_adjoint(const or_params *p, const double *g, const double *h, const double *phi, const double *c,
                     double *gb, double *hb, double *phib, double *cb, double *pb)
 {
+    if (p->h_lattice || p->h_eq_alt) return -2;   /* the adjoint covers the main scheme only */
     lattice L = get_lattice(p->dim);
     long N = (long)p->nx * p->ny * p->nz;
     int q = L.q;
@@ -670,6 +730,7 @@ int or_step_adjoint(const or_params *p, const double *g, const double *h, const 
 int or_init_adjoint(const or_params *p, const double *phi0, const double *c0, const double *gb, const double *hb,
                     double *phib, double *cb, double *pb)
 {
+    if (p->h_lattice || p->h_eq_alt) return -2;
     lattice L = get_lattice(p->dim);
     long N = (long)p->nx * p->ny * p->nz;
     int q = L.q;

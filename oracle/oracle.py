@@ -84,14 +84,16 @@ class _CParams(ctypes.Structure):
                 ("c_s_co", ctypes.c_double), ("c_l_co", ctypes.c_double),
                 ("mu_eq", ctypes.c_double), ("counter_term", ctypes.c_int),
                 ("anti_trapping", ctypes.c_int), ("a_at", ctypes.c_double),
-                ("eps_n", ctypes.c_double)]
+                ("eps_n", ctypes.c_double), ("h_lattice", ctypes.c_int), ("h_eq_alt", ctypes.c_int)]
 
 
 @dataclass
 class OracleParams:
     """Model parameters in lattice units (dx = dt = 1).
 
-    M_phi = tau_g / 3 (Sec. 3.2) and gamma = 3 / tau_h (Sec. 3.3)."""
+    M_phi = tau_g / 3 (Sec. 3.2) and gamma = 3 / tau_h (Sec. 3.3).  h_lattice = 1
+    puts h on D2Q5 / D3Q7 (xi_s^2 = 1/3); h_eq_alt = 1 uses the alternative
+    equilibrium of Eq. Seq_Concent_Alt with H = 0 (Sec. 3.3)."""
     nx: int
     ny: int
     nz: int = 1
@@ -109,6 +111,8 @@ class OracleParams:
     anti_trapping: int = 0
     a_at: float = 0.25
     eps_n: float = 1e-12
+    h_lattice: int = 0
+    h_eq_alt: int = 0
 
     @property
     def dim(self) -> int:
@@ -117,6 +121,16 @@ class OracleParams:
     @property
     def shape(self):
         return (self.nz, self.ny, self.nx)
+
+    @property
+    def q(self) -> int:
+        return 19 if self.dim == 3 else 9
+
+    @property
+    def q_h(self) -> int:
+        if self.h_lattice:
+            return 7 if self.dim == 3 else 5
+        return self.q
 
     def _c(self) -> _CParams:
         c = _CParams()
@@ -128,6 +142,7 @@ class OracleParams:
         c.c_s_co, c.c_l_co, c.mu_eq = self.c_s_co, self.c_l_co, self.mu_eq
         c.counter_term, c.anti_trapping = int(self.counter_term), int(self.anti_trapping)
         c.a_at, c.eps_n = self.a_at, self.eps_n
+        c.h_lattice, c.h_eq_alt = int(self.h_lattice), int(self.h_eq_alt)
         return c
 
 
@@ -141,7 +156,7 @@ class _CParamsCS(ctypes.Structure):
                 ("c_s_co", ctypes.c_double * 2), ("c_l_co", ctypes.c_double * 2),
                 ("mu_eq", ctypes.c_double * 2), ("counter_term", ctypes.c_int),
                 ("anti_trapping", ctypes.c_int), ("a_at", ctypes.c_double * 2),
-                ("eps_n", ctypes.c_double * 2)]
+                ("eps_n", ctypes.c_double * 2), ("h_lattice", ctypes.c_int), ("h_eq_alt", ctypes.c_int)]
 
 
 def _dp(a: np.ndarray):
@@ -149,13 +164,14 @@ def _dp(a: np.ndarray):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
-def lattice_tables(dim: int):
-    """(e [q,3] int, w [q], opp [q]) of the oracle's lattice."""
+def lattice_tables(code: int):
+    """(e [q,3] int, w [q], opp [q]) of an oracle lattice: code 2 D2Q9, 3 D3Q19,
+    5 D2Q5, 7 D3Q7."""
     lib = _load()
     e = (ctypes.c_int * 57)()
     w = np.zeros(19)
     opp = (ctypes.c_int * 19)()
-    q = lib.or_lattice(dim, e, _dp(w), opp)
+    q = lib.or_lattice(code, e, _dp(w), opp)
     return (np.array(e[:3 * q], dtype=np.int64).reshape(q, 3), w[:q].copy(),
             np.array(opp[:q], dtype=np.int64))
 
@@ -176,13 +192,13 @@ class Oracle:
     def __init__(self, p: OracleParams, phi0: np.ndarray, c0: np.ndarray):
         self.p = p
         self._cp = p._c()
-        q = 19 if p.dim == 3 else 9
+        q = p.q
         self.q = q
         shp = p.shape
         self.phi = np.zeros(shp)
         self.c = np.zeros(shp)
         self.g = np.zeros((q,) + shp)
-        self.h = np.zeros((q,) + shp)
+        self.h = np.zeros((p.q_h,) + shp)
         phi0 = np.ascontiguousarray(phi0, dtype=np.float64).reshape(shp)
         c0 = np.ascontiguousarray(c0, dtype=np.float64).reshape(shp)
         rc = _load().or_init(ctypes.byref(self._cp), _dp(phi0), _dp(c0), _dp(self.g),
@@ -199,9 +215,9 @@ class Oracle:
         o = cls.__new__(cls)
         o.p = p
         o._cp = p._c()
-        o.q = 19 if p.dim == 3 else 9
+        o.q = p.q
         o.g = np.ascontiguousarray(g, dtype=np.float64).reshape((o.q,) + p.shape).copy()
-        o.h = np.ascontiguousarray(h, dtype=np.float64).reshape((o.q,) + p.shape).copy()
+        o.h = np.ascontiguousarray(h, dtype=np.float64).reshape((p.q_h,) + p.shape).copy()
         o.phi = np.ascontiguousarray(phi, dtype=np.float64).reshape(p.shape).copy()
         o.c = np.ascontiguousarray(c, dtype=np.float64).reshape(p.shape).copy()
         o.t = 0
@@ -286,6 +302,8 @@ def step_adjoint(p: OracleParams, g, h, phi, c, gb, hb, phib, cb):
     st = [np.ascontiguousarray(a, dtype=np.float64) for a in (g, h, phi, c)]
     pb = np.zeros(4)
     rc = _load().or_step_adjoint(ctypes.byref(cp), *[_dp(a) for a in st], *[_dp(a) for a in arrs], _dp(pb))
+    if rc == -2:
+        raise NotImplementedError("the oracle adjoint covers h on the g lattice with H_k only")
     if rc != 0:
         raise MemoryError("oracle adjoint failed")
     return (*arrs, pb)
@@ -303,6 +321,8 @@ def init_adjoint(p: OracleParams, phi0, c0, gb, hb, phib, cb):
     pb = np.zeros(4)
     rc = _load().or_init_adjoint(ctypes.byref(cp), _dp(phi0), _dp(c0), _dp(gb), _dp(hb), _dp(phib), _dp(cb),
                                  _dp(pb))
+    if rc == -2:
+        raise NotImplementedError("the oracle adjoint covers h on the g lattice with H_k only")
     if rc != 0:
         raise MemoryError("oracle adjoint failed")
     return phib, cb, pb
@@ -339,6 +359,7 @@ def _cs_params(p: OracleParams, dparams, h):
         getattr(c, name)[0] = getattr(p, name)
         getattr(c, name)[1] = h * d.get(name, 0.0)
     c.counter_term, c.anti_trapping = int(p.counter_term), int(p.anti_trapping)
+    c.h_lattice, c.h_eq_alt = int(p.h_lattice), int(p.h_eq_alt)
     return c
 
 
@@ -348,12 +369,12 @@ def tangent_trajectory(p: OracleParams, phi0, c0, nsteps, dphi0=None, dc0=None, 
     lib = _load_cs()
     cp = _cs_params(p, dparams, h)
     shp = p.shape
-    q = 19 if p.dim == 3 else 9
+    q = p.q
     z = lambda a: np.zeros(shp) if a is None else np.asarray(a, dtype=np.float64).reshape(shp)
     phi0c = np.ascontiguousarray(np.asarray(phi0, dtype=np.float64).reshape(shp) + 1j * h * z(dphi0))
     c0c = np.ascontiguousarray(np.asarray(c0, dtype=np.float64).reshape(shp) + 1j * h * z(dc0))
     g = np.zeros((q,) + shp, complex)
-    hh = np.zeros((q,) + shp, complex)
+    hh = np.zeros((p.q_h,) + shp, complex)
     phi = np.zeros(shp, complex)
     c = np.zeros(shp, complex)
     P = lambda a: a.ctypes.data

@@ -58,6 +58,8 @@ class ModelParams:
     anti_trapping: int = 0
     a_at: float = 0.25
     eps_n: float = 1e-12
+    h_lattice: int = 0             # 1: h on D2Q5 / D3Q7 (Sec. 3.1)
+    h_eq_alt: int = 0              # 1: alternative equilibrium with H = 0 (Sec. 3.3)
 
     @property
     def shape(self):
