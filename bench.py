@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=20, help="steps of the FP64 comparison run")
     ap.add_argument("--dev16-steps", type=int, default=50, help="timed steps of each 16-bit storage run (0 = skip)")
+    ap.add_argument("--hvar-steps", type=int, default=100,
+                    help="timed steps of each variant of the composition scheme (h on D3Q7, h^eq,alt; 0 = skip)")
     ap.add_argument("--e4-steps", type=int, default=10000,
                     help="steps of the paper's 1024^2 porous experiment, timed in FP64 and FP32 (0 = skip)")
     ap.add_argument("--adj-steps", type=int, default=2000, help="steps of the 128^3 adjoint run (0 = skip)")
@@ -518,6 +520,36 @@ def run_ours(args):
                         "kernel_ms": {"k_phi_step": kp / args.dev16_steps, "k_c_step": kc / args.dev16_steps},
                         "mass_drift": (m0 - tgt) / tgt}
         extra["dev16"] = dev
+
+    # the two variants of the composition scheme of Sec. 3 on the same workload:
+    # h on D3Q7 (fewer bytes per node) and the alternative equilibrium h^eq,alt
+    if prec == "fp32" and args.hvar_steps > 0:
+        import dataclasses
+        hv = {}
+        for name, hl, alt in (("h_d3q7", 1, 0), ("h_eq_alt", 0, 1), ("h_d3q7_eq_alt", 1, 1)):
+            mv = dataclasses.replace(model, h_lattice=hl, h_eq_alt=alt)
+            sv = L.Simulation(mv, phi0, c0, precision="fp32", stream=stream.cuda_stream, lattice=L.LBPF_D3Q19,
+                              mass_every=1)
+            sv.step(3)
+            torch.cuda.synchronize()
+            av, bv = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            av.record(stream)
+            kp, kc, kr = sv.step_timed(args.hvar_steps)
+            bv.record(stream)
+            torch.cuda.synchronize()
+            msv = av.elapsed_time(bv) / args.hvar_steps
+            m0, tgt = sv.solute_mass()
+            sv.close()
+            qh = 7 if hl else 19
+            bp, bc = 2 * q * 4 + 2 * 4, 2 * qh * 4
+            kcm = kc / args.hvar_steps
+            hv[name] = {"h_lattice": "D3Q7" if hl else "D3Q19", "h_eq_alt": alt,
+                        "ms_per_step": msv, "mlups": N / (msv * 1e-3) / 1e6,
+                        "bytes_per_node": bp + bc, "step_frac": (bp + bc) * N / (msv * 1e-3) / 1e9 / hbm,
+                        "k_c_step_frac": bc * N / (kcm * 1e-3) / 1e9 / hbm,
+                        "kernel_ms": {"k_phi_step": kp / args.hvar_steps, "k_c_step": kcm},
+                        "speedup_vs_main": ms_per_step / msv, "mass_drift": (m0 - tgt) / tgt}
+        extra["h_variants"] = hv
 
     e4 = None
     if args.e4_steps > 0 and prec == "fp32":

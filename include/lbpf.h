@@ -19,6 +19,10 @@
  *     (Eq. SourceTerm_LBE_h), equilibrium h^eq (Eq. Heq_Composition), BGK
  *     collision and streaming (Eq. LBE_Composition), c = sum_k h_k
  *     (Eq. Moment0_LBM_Concent).
+ * Two variants of the composition scheme named in Sec. 3 are selectable: the
+ * alternative equilibrium h^eq,alt that carries the flux with H_k = 0
+ * (Eq. LBE_Concent_Alt, Eq. Seq_Concent_Alt), and h on the small lattice of the
+ * paper's code (D2Q5 / D3Q7, Sec. 3.1) while g keeps D2Q9 / D3Q19.
  *
  * Conventions shared by every entry point:
  *   - Every call returns an lbpf_status and never throws across the ABI.
@@ -58,7 +62,9 @@ typedef enum {
     LBPF_EUNSUPPORTED = 7 /* option combination not built */
 } lbpf_status;
 
-typedef enum { LBPF_D2Q9 = 0, LBPF_D3Q19 = 1 } lbpf_lattice;
+/* Lattices of g (and by default of h): D2Q9, D3Q19.  D2Q5 and D3Q7 only carry
+ * h (lbpf_params.h_lattice = 1) and are listed for lbpf_lattice_info. */
+typedef enum { LBPF_D2Q9 = 0, LBPF_D3Q19 = 1, LBPF_D2Q5 = 2, LBPF_D3Q7 = 3 } lbpf_lattice;
 
 /* Storage and arithmetic of the populations and fields.  FP64: all FP64.
  * FP32: FP32 storage and arithmetic.  The *DEV modes store each population as a
@@ -100,6 +106,15 @@ typedef struct {
                                     lbpf_solute_mass); FP32 and 16-bit modes want 1 */
     int32_t checkpoint_every;    /* 0: no adjoint; k > 0: record the state every k
                                     steps for lbpf_adjoint_step (FP64 and FP32 only) */
+    int32_t h_lattice;           /* 0: h on the lattice of g; 1: h on the small lattice,
+                                    D2Q5 with D2Q9 or D3Q7 with D3Q19 (Sec. 3.1), weights
+                                    1/3, 1/6 and 0, 1/6 so that xi_s^2 = 1/3 and
+                                    tau_h = 3 dt / (gamma dx^2) still hold */
+    int32_t h_eq_alt;            /* 0: h^eq with the source H_k (Eq. Heq_Composition,
+                                    Eq. SourceTerm_LBE_h); 1: the alternative
+                                    equilibrium h^eq,alt_k = w_k [gamma D mu + e_k.F /
+                                    xi_s^2] with H_k = 0 (Eq. Seq_Concent_Alt), F = mu D'
+                                    grad phi + j_at */
 } lbpf_params;
 
 typedef struct lbpf_ctx lbpf_ctx;
@@ -107,19 +122,23 @@ typedef struct lbpf_ctx lbpf_ctx;
 /* Fill *p with defaults: 2-D D2Q9 64x64 periodic, FP64, dx = dt = 1,
  * tau_g = tau_h = 0.36, W = 3, lambda = 0, D_l = D_s = 0.1, c_s^co = 1,
  * c_l^co = 0.5, mu_eq = 0.4, counter term on, anti-trapping off, a = -1 (auto),
- * eps_n = 1e-12.  Returns LBPF_EINVAL if p is NULL. */
+ * eps_n = 1e-12, h on the lattice of g with H_k (h_lattice = h_eq_alt = 0).
+ * Returns LBPF_EINVAL if p is NULL. */
 lbpf_status lbpf_default_params(lbpf_params *p);
 
 /* Create a context on the current CUDA device: validate p, allocate the
  * populations (two ping-pong sets of g and h, SoA [k][z][y][x]) and the fields
  * phi^n, phi^{n+1}, c^n, c^{n+1}, copy phi0 and c0 (FP64, [nz][ny][nx]) and set
  * the populations to g_k = w_k phi0 - G_k/2 and h_k = h^eq_k - H_k/2 (the
- * variable change of Sec. 3.1 at equilibrium, H at dphi/dt = 0).
+ * variable change of Sec. 3.1 at equilibrium, H at dphi/dt = 0), or
+ * h_k = h^eq,alt_k with h_eq_alt = 1.
  * cuda_stream: a cudaStream_t (NULL = default stream).  On success *out owns
  * everything; on failure *out is NULL and nothing is leaked.
  * Errors: EINVAL (NULL pointers, sizes < 1, nz != 1 for D2Q9, a bounce-back
- * axis with fewer than 2 nodes, tau <= 0, W <= 0, D < 0, unknown enum),
- * ENOMEM, ECUDA, EUNSUPPORTED. */
+ * axis with fewer than 2 nodes, tau <= 0, W <= 0, D < 0, unknown enum,
+ * h_lattice or h_eq_alt not 0 / 1), ENOMEM, ECUDA, EUNSUPPORTED
+ * (checkpoint_every > 0 with h_lattice = 1 or h_eq_alt = 1: the adjoint covers
+ * the main scheme only). */
 lbpf_status lbpf_create(const lbpf_params *p, const double *phi0, const double *c0,
                         int32_t ptr_is_device, void *cuda_stream, lbpf_ctx **out);
 
@@ -157,8 +176,10 @@ lbpf_status lbpf_get_fields(lbpf_ctx *ctx, double *phi, double *c, double *mu,
                             int32_t ptr_is_device);
 
 /* Copy the populations g and h (post-streaming, before the next collision),
- * FP64 [q][nz][ny][nx], q = 9 (D2Q9) or 19 (D3Q19).  For the deviation-storage
- * modes the stored deviations are expanded back to full populations.
+ * FP64 [q][nz][ny][nx]: g with q = 9 (D2Q9) or 19 (D3Q19), h with the q of its
+ * lattice (9 / 19, or 5 / 7 with h_lattice = 1).  For the deviation-storage
+ * modes the stored deviations are expanded back to full populations.  With
+ * h_eq_alt = 0 the h returned are the shifted populations h~ of Sec. 3.3.
  * Either pointer may be NULL.  Synchronises the stream. */
 lbpf_status lbpf_get_populations(lbpf_ctx *ctx, double *g, double *h, int32_t ptr_is_device);
 
@@ -179,9 +200,10 @@ lbpf_status lbpf_step_timed(lbpf_ctx *ctx, int64_t nsteps, double *kernel_ms);
 lbpf_status lbpf_fp64_fma_rate(void *cuda_stream, double *tflops);
 
 /* Lattice table of the population ordering used by lbpf_get_populations:
- * *q = 9 or 19; e (optional, int32 [q][3]) the link vectors; w (optional,
- * [q]) the weights.  D2Q9 follows Sec. 3.1 (e0 = 0, e1..e4 axis links
- * (1,0),(0,1),(-1,0),(0,-1), e5..e8 diagonals (1,1),(-1,1),(-1,-1),(1,-1)).
+ * *q = 9, 19, 5 or 7; e (optional, int32 [q][3]) the link vectors; w
+ * (optional, [q]) the weights.  D2Q9 follows Sec. 3.1 (e0 = 0, e1..e4 axis
+ * links (1,0),(0,1),(-1,0),(0,-1), e5..e8 diagonals (1,1),(-1,1),(-1,-1),
+ * (1,-1)); D2Q5 and D3Q7 are the first 5 / 7 links of D2Q9 / D3Q19.
  * Needs no GPU.  Errors: EINVAL for an unknown lattice or q == NULL. */
 lbpf_status lbpf_lattice_info(int32_t lattice, int32_t *q, int32_t *e, double *w);
 
@@ -192,7 +214,8 @@ lbpf_status lbpf_lattice_info(int32_t lattice, int32_t *q, int32_t *e, double *w
  * all instances, so the work is balanced whatever the size mix.  p[i], phi0[i],
  * c0[i] describe instance i exactly as for lbpf_create (each with its own
  * sizes, walls and parameters); all instances must be D2Q9 with the same
- * precision, mass_every = 0, checkpoint_every = 0 and 9 nx ny x (bytes per
+ * precision, mass_every = 0, checkpoint_every = 0, h_lattice = h_eq_alt = 0
+ * and 9 nx ny x (bytes per
  * stored value: 8 FP64, 4 FP32, 2 for 16-bit storage) < 2^31 (the kernels
  * address within an instance with 32-bit byte offsets).  The fields are copied;
  * ptr_is_device says where phi0[i] and c0[i] live.  lbpf_step,
@@ -201,7 +224,7 @@ lbpf_status lbpf_lattice_info(int32_t lattice, int32_t *q, int32_t *e, double *w
  * LBPF_EUNSUPPORTED (use the calls below).
  * Errors: EINVAL (NULL pointers, n < 1, an invalid or oversized instance: the
  * message names it), EUNSUPPORTED (non-D2Q9 instance, mass_every != 0,
- * checkpoint_every != 0), ENOMEM, ECUDA. */
+ * checkpoint_every != 0, h_lattice != 0, h_eq_alt != 0), ENOMEM, ECUDA. */
 lbpf_status lbpf_create_batch(const lbpf_params *p, int32_t n, const double *const *phi0,
                               const double *const *c0, int32_t ptr_is_device, void *cuda_stream,
                               lbpf_ctx **out);

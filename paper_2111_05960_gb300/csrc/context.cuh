@@ -60,7 +60,8 @@ struct lbpf_ctx {
     lbpf::StepParams sp;
     lbpf::KParams kp;
     lbpf::KParams kpm;             // the marching kernels' view (2-D: rows as z-planes)
-    int q = 0;
+    int q = 0;                     // populations of g
+    int qh = 0;                    // populations of h (q, or 5 / 7 on the small lattice)
     size_t real_size = 0, store_size = 0;
     cudaStream_t stream = nullptr;
     int device = 0;

@@ -13,6 +13,12 @@
 // w = 4/9, 1/9, 1/36.  D3Q19 (named among the lattices of the paper's code in
 // Sec. 3.1) is used for 3-D: rest (1/3), six face links (1/18), twelve edge
 // links (1/36), with opposite directions stored next to each other.
+//
+// D2Q5 and D3Q7 (also named in Sec. 3.1) can carry the composition populations
+// h: the rest and axis links of D2Q9 / D3Q19, in the same order, with weights
+// for xi_s^2 = 1/3 as on the full lattices (so tau_h = 3 / gamma is unchanged):
+// D2Q5 w = 1/3, 1/6; D3Q7 w = 0, 1/6.  Their weights are m_k / 6 (DEN = 6),
+// again with unit m_k on the moving links.
 #pragma once
 
 namespace lbpf {
@@ -20,6 +26,7 @@ namespace lbpf {
 struct D2Q9 {
     static constexpr int D = 2;
     static constexpr int Q = 9;
+    static constexpr int DEN = 36;          // w_k = m_k / DEN
     static constexpr bool FLAT_Y = false;   // has links along y
     __host__ __device__ static constexpr int ex(int k) {
         return (k == 1 || k == 5 || k == 8) ? 1 : ((k == 3 || k == 6 || k == 7) ? -1 : 0);
@@ -41,6 +48,7 @@ struct D2Q9 {
 struct D3Q19 {
     static constexpr int D = 3;
     static constexpr int Q = 19;
+    static constexpr int DEN = 36;
     static constexpr bool FLAT_Y = false;
     // k: 1..6 faces +x -x +y -y +z -z; 7..18 edges
     // (1,1,0) (-1,-1,0) (1,-1,0) (-1,1,0) (1,0,1) (-1,0,-1) (1,0,-1) (-1,0,1)
@@ -74,6 +82,7 @@ struct D3Q19 {
 struct D2Q9R {
     static constexpr int D = 3;               // marched like a 3-D lattice
     static constexpr int Q = 9;
+    static constexpr int DEN = 36;
     static constexpr bool FLAT_Y = true;      // no links along the (unit) y axis
     __host__ __device__ static constexpr int ex(int k) { return D2Q9::ex(k); }
     __host__ __device__ static constexpr int ey(int) { return 0; }
@@ -82,5 +91,33 @@ struct D2Q9R {
     __host__ __device__ static constexpr int opp(int k) { return D2Q9::opp(k); }
     __host__ __device__ static constexpr int m(int k) { return D2Q9::m(k); }
 };
+
+// Small lattices for h: the first Q links of the full lattice.
+template <class Full, int QH, int M0>
+struct SmallLattice {
+    static constexpr int D = Full::D;
+    static constexpr int Q = QH;
+    static constexpr int DEN = 6;
+    static constexpr bool FLAT_Y = Full::FLAT_Y;
+    __host__ __device__ static constexpr int ex(int k) { return Full::ex(k); }
+    __host__ __device__ static constexpr int ey(int k) { return Full::ey(k); }
+    __host__ __device__ static constexpr int ez(int k) { return Full::ez(k); }
+    __host__ __device__ static constexpr int m(int k) { return k == 0 ? M0 : 1; }
+    __host__ __device__ static constexpr double w(int k) { return m(k) / 6.0; }
+    __host__ __device__ static constexpr int opp(int k) { return Full::opp(k); }
+};
+using D2Q5 = SmallLattice<D2Q9, 5, 2>;     // w = 1/3, 1/6
+using D2Q5R = SmallLattice<D2Q9R, 5, 2>;   // the same in the row-marching view
+using D3Q7 = SmallLattice<D3Q19, 7, 0>;    // w = 0, 1/6
+
+// The small lattice of h that goes with a full one.
+template <class L>
+struct SmallOf;
+template <>
+struct SmallOf<D2Q9> { using type = D2Q5; };
+template <>
+struct SmallOf<D2Q9R> { using type = D2Q5R; };
+template <>
+struct SmallOf<D3Q19> { using type = D3Q7; };
 
 }  // namespace lbpf

@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <string>
 #include <vector>
 
@@ -124,19 +125,22 @@ struct TileCfg<D3Q19, true> {
     static constexpr int BX = 32, BY = LBPF_BY3_F64, ZCH = LBPF_ZCH3_F64, MINB = LBPF_MINB3_F64;
 };
 
-template <class L, class SP>
+// HS: h on the small lattice of L (D2Q5 / D3Q7) instead of L itself.
+template <class L, class SP, bool HS = false>
 struct Impl {
     using R = typename SP::real;
     using S = typename SP::store_t;
     using T = TileCfg<L, sizeof(R) == 8>;
     using ML = typename T::ML;              // the lattice as the marching kernels see it
+    using MLH = typename std::conditional<HS, typename SmallOf<ML>::type, ML>::type;   // h, marching view
+    using LH = typename std::conditional<HS, typename SmallOf<L>::type, L>::type;      // h, grid view
     static constexpr int BX = T::BX, BY = T::BY, ZCH = T::ZCH, MINB = T::MINB;
     static constexpr size_t smem_phi = march_smem<ML, SP, BY, ZCH, BX>(true);
     static constexpr size_t smem_c = march_smem<ML, SP, BY, ZCH, BX>(false);
     template <bool W>
     static constexpr auto kphi() { return k_phi_step<ML, SP, BY, ZCH, MINB, W, BX>; }
     template <bool W>
-    static constexpr auto kc() { return k_c_step<ML, SP, BY, ZCH, MINB, W, BX>; }
+    static constexpr auto kc() { return k_c_step<ML, SP, BY, ZCH, MINB, W, BX, MLH>; }
 
     static lbpf_status prepare(lbpf_ctx* ctx) {
         LBPF_CUDA(ctx, cudaFuncSetAttribute(kphi<true>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_phi));
@@ -178,14 +182,14 @@ struct Impl {
     }
     static void launch_init(lbpf_ctx* ctx) {
         const long long N = ctx->sp.N;
-        k_init<L, SP><<<(unsigned)((N + 255) / 256), 256, 0, ctx->stream>>>(
+        k_init<L, SP, LH><<<(unsigned)((N + 255) / 256), 256, 0, ctx->stream>>>(
             ctx->kp, (const R*)ctx->phi[ctx->cur], (R*)ctx->c[ctx->cur], (S*)ctx->g[ctx->cur],
             (S*)ctx->h[ctx->cur]);
     }
     static void launch_pops_out(lbpf_ctx* ctx, double* g, double* h) {
         const long long N = ctx->sp.N;
         const int cur = ctx->cur;
-        k_pops_out<L, SP><<<(unsigned)((N + 255) / 256), 256, 0, ctx->stream>>>(
+        k_pops_out<L, SP, LH><<<(unsigned)((N + 255) / 256), 256, 0, ctx->stream>>>(
             ctx->kp, (const R*)ctx->phi[cur], (const R*)ctx->c[cur], (const S*)ctx->g[cur],
             (const S*)ctx->h[cur], g, h);
     }
@@ -199,7 +203,7 @@ struct Impl {
         launch_corr_p(ctx, ctx->corr, ctx->c[cur_after], ctx->h[cur_after]);
     }
     static void launch_pop_mass(lbpf_ctx* ctx) {
-        k_pop_mass<L, SP><<<ctx->mass_blocks, kMassThreads, 0, ctx->stream>>>(
+        k_pop_mass<LH, SP><<<ctx->mass_blocks, kMassThreads, 0, ctx->stream>>>(
             ctx->kp, (const R*)ctx->phi[ctx->cur], (const R*)ctx->c[ctx->cur], (const S*)ctx->h[ctx->cur],
             ctx->partials);
         k_mass_final<<<1, kMassThreads, 0, ctx->stream>>>(ctx->partials, ctx->mass_blocks, ctx->mass_out);
@@ -216,22 +220,20 @@ struct Impl {
     }
 };
 
-const Dispatch* pick(int lattice, int precision) {
-    if (lattice == LBPF_D2Q9) {
-        switch (precision) {
-            case LBPF_FP64: return Impl<D2Q9, StoreF64>::table();
-            case LBPF_FP32: return Impl<D2Q9, StoreF32>::table();
-            case LBPF_FP32_BF16DEV: return Impl<D2Q9, StoreBF16Dev>::table();
-            case LBPF_FP32_FP16DEV: return Impl<D2Q9, StoreF16Dev>::table();
-        }
-    } else if (lattice == LBPF_D3Q19) {
-        switch (precision) {
-            case LBPF_FP64: return Impl<D3Q19, StoreF64>::table();
-            case LBPF_FP32: return Impl<D3Q19, StoreF32>::table();
-            case LBPF_FP32_BF16DEV: return Impl<D3Q19, StoreBF16Dev>::table();
-            case LBPF_FP32_FP16DEV: return Impl<D3Q19, StoreF16Dev>::table();
-        }
+template <class L, bool HS>
+const Dispatch* pick_storage(int precision) {
+    switch (precision) {
+        case LBPF_FP64: return Impl<L, StoreF64, HS>::table();
+        case LBPF_FP32: return Impl<L, StoreF32, HS>::table();
+        case LBPF_FP32_BF16DEV: return Impl<L, StoreBF16Dev, HS>::table();
+        case LBPF_FP32_FP16DEV: return Impl<L, StoreF16Dev, HS>::table();
     }
+    return nullptr;
+}
+
+const Dispatch* pick(int lattice, int precision, bool h_small) {
+    if (lattice == LBPF_D2Q9) return h_small ? pick_storage<D2Q9, true>(precision) : pick_storage<D2Q9, false>(precision);
+    if (lattice == LBPF_D3Q19) return h_small ? pick_storage<D3Q19, true>(precision) : pick_storage<D3Q19, false>(precision);
     return nullptr;
 }
 
@@ -263,6 +265,8 @@ lbpf_status lbpf_rt::validate(const lbpf_params* p, std::string& why) {
     if (p->anti_trapping && p->a_at < 0 && !(p->D_l > 0)) return bad("automatic a needs D_l > 0");
     if (p->mass_every < 0) return bad("mass_every must be >= 0");
     if (p->checkpoint_every < 0) return bad("checkpoint_every must be >= 0");
+    if (p->h_lattice != 0 && p->h_lattice != 1) return bad("h_lattice must be 0 or 1");
+    if (p->h_eq_alt != 0 && p->h_eq_alt != 1) return bad("h_eq_alt must be 0 or 1");
     return LBPF_OK;
 }
 
@@ -287,6 +291,8 @@ StepParams lbpf_rt::lattice_units(const lbpf_params* p) {
     s.a_at = p->anti_trapping ? a : 0.0;
     s.eps2 = p->eps_n * p->eps_n;
     s.counter_term = p->counter_term ? 1 : 0;
+    s.h_den = p->h_lattice ? 6 : 36;     // w_k = m_k / DEN on the h lattice
+    s.h_eq_alt = p->h_eq_alt ? 1 : 0;
     return s;
 }
 
@@ -491,10 +497,12 @@ lbpf_status lbpf_create(const lbpf_params* p, const double* phi0, const double* 
     if (!p || !phi0 || !c0) return fail(nullptr, LBPF_EINVAL, "NULL params or field pointer");
     std::string why;
     if (validate(p, why) != LBPF_OK) return fail(nullptr, LBPF_EINVAL, why);
-    const Dispatch* ops = pick(p->lattice, p->precision);
+    const Dispatch* ops = pick(p->lattice, p->precision, p->h_lattice != 0);
     if (!ops) return fail(nullptr, LBPF_EUNSUPPORTED, "lattice/precision not built");
     const AdjDispatch* aops = nullptr;
     if (p->checkpoint_every > 0) {
+        if (p->h_lattice || p->h_eq_alt)
+            return fail(nullptr, LBPF_EUNSUPPORTED, "the adjoint covers h on the lattice of g with H_k only");
         aops = pick_adjoint(p->lattice, p->precision);
         if (!aops) return fail(nullptr, LBPF_EUNSUPPORTED, "the adjoint is built for FP64 and FP32 storage only");
         if (p->ny > 8 * 65535) return fail(nullptr, LBPF_EUNSUPPORTED, "the adjoint needs ny <= 524280");
@@ -505,6 +513,7 @@ lbpf_status lbpf_create(const lbpf_params* p, const double* phi0, const double* 
     ctx->p = *p;
     ctx->sp = lattice_units(p);
     ctx->q = p->lattice == LBPF_D3Q19 ? 19 : 9;
+    ctx->qh = p->h_lattice ? (p->lattice == LBPF_D3Q19 ? 7 : 5) : ctx->q;
     ctx->kp = make_kparams(p);
     ctx->kpm = march_kparams(ctx->kp, p->lattice);
     ctx->ops = ops;
@@ -526,7 +535,7 @@ lbpf_status lbpf_create(const lbpf_params* p, const double* phi0, const double* 
     if (e != cudaSuccess) { cuda_fail(ctx, e, "cudaGetDevice"); return abort_create(LBPF_ECUDA); }
     for (int i = 0; i < 2; ++i) {
         if ((st = alloc(ctx, &ctx->g[i], ctx->store_size * ctx->q * N, "g populations")) != LBPF_OK) return abort_create(st);
-        if ((st = alloc(ctx, &ctx->h[i], ctx->store_size * ctx->q * N, "h populations")) != LBPF_OK) return abort_create(st);
+        if ((st = alloc(ctx, &ctx->h[i], ctx->store_size * ctx->qh * N, "h populations")) != LBPF_OK) return abort_create(st);
         if ((st = alloc(ctx, &ctx->phi[i], ctx->real_size * N, "phi field")) != LBPF_OK) return abort_create(st);
         if ((st = alloc(ctx, &ctx->c[i], ctx->real_size * N, "c field")) != LBPF_OK) return abort_create(st);
     }
@@ -712,9 +721,10 @@ lbpf_status lbpf_get_populations(lbpf_ctx* ctx, double* g, double* h, int32_t pt
     if (ctx->is_batch) return fail(ctx, LBPF_EUNSUPPORTED, "a batch context: use the lbpf_batch_* calls");
     if (ctx->poisoned) return fail(ctx, LBPF_ESTATE, "context poisoned by an earlier error");
     const size_t bytes = sizeof(double) * ctx->q * (size_t)ctx->sp.N;
+    const size_t hbytes = sizeof(double) * ctx->qh * (size_t)ctx->sp.N;
     double *dg = g, *dh = h, *tmp = nullptr;
     if (!ptr_is_device && (g || h)) {
-        lbpf_status st = alloc(ctx, (void**)&tmp, 2 * bytes, "population export buffer");
+        lbpf_status st = alloc(ctx, (void**)&tmp, bytes + hbytes, "population export buffer");
         if (st != LBPF_OK) return st;
         dg = g ? tmp : nullptr;
         dh = h ? tmp + ctx->q * (size_t)ctx->sp.N : nullptr;
@@ -724,7 +734,7 @@ lbpf_status lbpf_get_populations(lbpf_ctx* ctx, double* g, double* h, int32_t pt
     cudaError_t e = cudaSuccess;
     if (st == LBPF_OK && !ptr_is_device) {
         if (g && e == cudaSuccess) e = cudaMemcpyAsync(g, dg, bytes, cudaMemcpyDeviceToHost, ctx->stream);
-        if (h && e == cudaSuccess) e = cudaMemcpyAsync(h, dh, bytes, cudaMemcpyDeviceToHost, ctx->stream);
+        if (h && e == cudaSuccess) e = cudaMemcpyAsync(h, dh, hbytes, cudaMemcpyDeviceToHost, ctx->stream);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (tmp) cudaFree(tmp);
@@ -790,6 +800,18 @@ lbpf_status lbpf_lattice_info(int32_t lattice, int32_t* q, int32_t* e, double* w
         for (int k = 0; k < 19; ++k) {
             if (e) { e[3 * k] = D3Q19::ex(k); e[3 * k + 1] = D3Q19::ey(k); e[3 * k + 2] = D3Q19::ez(k); }
             if (w) w[k] = D3Q19::w(k);
+        }
+    } else if (lattice == LBPF_D2Q5) {
+        *q = 5;
+        for (int k = 0; k < 5; ++k) {
+            if (e) { e[3 * k] = D2Q5::ex(k); e[3 * k + 1] = D2Q5::ey(k); e[3 * k + 2] = 0; }
+            if (w) w[k] = D2Q5::w(k);
+        }
+    } else if (lattice == LBPF_D3Q7) {
+        *q = 7;
+        for (int k = 0; k < 7; ++k) {
+            if (e) { e[3 * k] = D3Q7::ex(k); e[3 * k + 1] = D3Q7::ey(k); e[3 * k + 2] = D3Q7::ez(k); }
+            if (w) w[k] = D3Q7::w(k);
         }
     } else {
         return fail(nullptr, LBPF_EINVAL, "unknown lattice");

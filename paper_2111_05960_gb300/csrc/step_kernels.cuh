@@ -52,6 +52,8 @@ struct StepParams {
     double a_at;        // a of j_at, 0 when anti-trapping is off
     double eps2;        // eps_n^2
     int counter_term;
+    int h_den;          // DEN of the h lattice: 36 (D2Q9 / D3Q19) or 6 (D2Q5 / D3Q7)
+    int h_eq_alt;       // 1: h^eq,alt with H_k = 0 (Eq. Seq_Concent_Alt)
 };
 
 // Derived constants of one simulation in the compute type, precomputed on the
@@ -64,7 +66,10 @@ template <typename R>
 struct Coef {
     R mu_eq, c_l, c_s, kS, kst, kdw, kct, D_l, D_s, Dp, gamma, atk, omg, omh, eps2;
     R kct36;   // (1 - w_g/2) kct / 36: the counter-term vector per unit m_k
-    R kh36;    // (1 - w_h/2) gamma / 36: the flux vector of H per unit m_k
+    // the flux vector of the h collision per unit m_k of the h lattice (w_k =
+    // m_k / DEN): (1 - w_h/2) gamma / DEN for H_k (Eq. SourceTerm_LBE_h), or
+    // w_h / (xi_s^2 DEN) = 3 w_h / DEN for h^eq,alt (Eq. Seq_Concent_Alt)
+    R khw;
 };
 
 template <typename R>
@@ -80,7 +85,7 @@ __host__ Coef<R> make_coef(const StepParams& P) {
     c.atk = R(P.a_at * P.W * (P.c_s - P.c_l));
     c.omg = R(P.omg); c.omh = R(P.omh); c.eps2 = R(P.eps2);
     c.kct36 = R((1.0 - 0.5 * P.omg) * (P.counter_term ? 4.0 / P.W : 0.0) / 36.0);
-    c.kh36 = R((1.0 - 0.5 * P.omh) * P.gamma / 36.0);
+    c.khw = R(P.h_eq_alt ? 3.0 * P.omh / P.h_den : (1.0 - 0.5 * P.omh) * P.gamma / P.h_den);
     return c;
 }
 
@@ -225,17 +230,17 @@ __device__ __forceinline__ double rsqrt_reg<double>(double g2, double eps2) { re
 template <>
 __device__ __forceinline__ float rsqrt_reg<float>(float g2, float eps2) { return rsqrtf(g2 + eps2); }
 
-// x / 36 for the weights w_k = m_k / 36.  FP32: correctly rounded, so the
+// x / 36 for the weights w_k = m_k / 36 (x / DEN in general).  FP32: correctly rounded, so the
 // rounding of each node's per-unit quantity is unbiased and the m_k-weighted
 // links conserve it (see lattice.cuh).  FP64: a multiplication by 1/36, whose
 // ~1e-17 relative bias is far below anything FP64 resolves, at a fraction of
 // the cost of a double division (the FP64 step is bound by the FP64 pipe).
+template <int DEN>
+__device__ __forceinline__ float divw(float x) { return x / float(DEN); }
+template <int DEN>
+__device__ __forceinline__ double divw(double x) { return x * (1.0 / DEN); }
 template <typename R>
-__device__ __forceinline__ R div36(R x);
-template <>
-__device__ __forceinline__ float div36<float>(float x) { return x / 36.0f; }
-template <>
-__device__ __forceinline__ double div36<double>(double x) { return x * (1.0 / 36.0); }
+__device__ __forceinline__ R div36(R x) { return divw<36>(x); }
 
 // G^st + G^dw: the isotropic part of G_k / w_k (Eq. SourceG_ST, Eq. SourceG_dw;
 // S_phi of Eq. SourceTerm_Coexistence with p' = 6 phi (1 - phi);
@@ -432,7 +437,7 @@ __device__ __forceinline__ void phi_ingredients(const StepParams& P, const Coef<
 
 // Ingredients of the h collision on one plane: P = gamma D mu and
 // beta_h = (1 - w_h/2) gamma (mu D' grad phi + j_at).
-template <class L, int BY, int BX, typename R>
+template <class L, class LH, int BY, int BX, typename R>
 __device__ __forceinline__ void c_ingredients(const StepParams& P, const Coef<R>& C, const R* cst, const R* pst,
                                               const R* pm, const R* p0, const R* pp, V4<R>* ing,
                                               const HaloOffsets<Geo<L, BY, BX>>& H) {
@@ -452,8 +457,8 @@ __device__ __forceinline__ void c_ingredients(const StepParams& P, const Coef<R>
         const R inv = rsqrt_reg<R>(gx * gx + gy * gy + gz_ * gz_, C.eps2);
         const R f = mu * C.Dp + C.atk * dphi * inv;        // F = (mu D' + j_at / |grad|) grad
         V4<R> v;
-        v.a = div36(p_term(C, ph, mu));                  // P per unit m_k
-        const R ff = C.kh36 * f;
+        v.a = divw<LH::DEN>(p_term(C, ph, mu));          // P per unit m_k of the h lattice
+        const R ff = C.khw * f;
         v.b = ff * gx; v.c = ff * gy; v.d = ff * gz_;
         ing[s] = v;
     }
@@ -578,7 +583,7 @@ __device__ __forceinline__ void pull_combine(const KParams& K, const Coef<typena
     constexpr int k0 = IS_PHI ? 0 : 1;
     if (!IS_PHI) {
         // rest population of h: h*_0 = (1 - w_h) h_0 + w_h h^eq_0 (H_0 = 0)
-        const R heq0 = st.cx - R(36 - L::m(0)) * i0[c1].a;   // h^eq_0 = c - (1 - w_0) P
+        const R heq0 = st.cx - R(L::DEN - L::m(0)) * i0[c1].a;   // h^eq_0 = c - (1 - w_0) P
         v[0] = keep * (SP::deviation ? st.old[0] + heq0 : st.old[0]) + om * heq0;
         sum = v[0];
         if (!hold) SP::store(byte_add(out, link_base<I>(K, 0)), 0, v[0], R(0));
@@ -624,10 +629,10 @@ __device__ __forceinline__ void pull_combine(const KParams& K, const Coef<typena
         moment_out[xi] = sum;                      // Eq. Moment0_LBM_Concent
         if (hold) {
             const R phin = phi_np1_in[xi];
-            const R Ps = div36(p_term(C, phin, closure_mu(C, phin, sum)));
+            const R Ps = divw<L::DEN>(p_term(C, phin, closure_mu(C, phin, sum)));
             // the mass regulated by the correction is that of the populations as
             // stored (quantised), i.e. of the values the next step loads
-            const R ref0 = sum - R(36 - L::m(0)) * Ps;
+            const R ref0 = sum - R(L::DEN - L::m(0)) * Ps;
             SP::store(byte_add(out, link_base<I>(K, 0)), 0, v[0], ref0);
             R ms = SP::stored(v[0], ref0), mcomp = R(0);
 #pragma unroll
@@ -664,7 +669,8 @@ __device__ __forceinline__ void block_mass_out(const MassAcc<R>& m, double* __re
 // One z-marching pass of either kernel.  The composition kernel also sums the
 // exact mass of the populations it writes into mass_partials (one FP64 value
 // per block) when that pointer is not null.
-template <class L, class SP, int BY, int ZCH, bool IS_PHI, bool WALLS, int BX = 32, typename I = long long>
+template <class L, class SP, int BY, int ZCH, bool IS_PHI, bool WALLS, int BX = 32, typename I = long long,
+          class LH = L>
 __device__ __forceinline__ void march(const KParams& K, const typename SP::store_t* __restrict__ fin,
                                       typename SP::store_t* __restrict__ fout,
                                       const typename SP::real* __restrict__ phi_n,
@@ -688,7 +694,11 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
     const bool active_xy = x < P.nx && y < P.ny;
     const bool inside2 = x0 >= 2 && x0 + G::BX + 2 <= P.nx && y0 >= G::OY2 && y0 + BY + G::OY2 <= P.ny;
     const bool inside1 = x0 >= 1 && x0 + G::BX + 1 <= P.nx && y0 >= G::OY1 && y0 + BY + G::OY1 <= P.ny;
-    PullState<L, SP, IS_PHI, WALLS, I> st;
+    // the composition kernel pulls h on LH (L, or its small lattice); the phi
+    // stencil and the ingredient window always follow L
+    static_assert(IS_PHI ? std::is_same<L, LH>::value : L::FLAT_Y == LH::FLAT_Y, "h lattice");
+    using LP = LH;
+    PullState<LP, SP, IS_PHI, WALLS, I> st;
     MassAcc<R> macc{R(0), R(0)};
 
     // the ring inputs of plane zg go to stage buffer zg & 1
@@ -705,8 +715,8 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
             phi_ingredients<L, BY, BX>(P, C, cst + b * G::P1, pm, p0, pp, sing + slot_i * G::P1, sA + slot_i * G::P1,
                                        halo);
         else
-            c_ingredients<L, BY, BX>(P, C, cst + b * G::P1, pst + b * G::P1, pm, p0, pp, sing + slot_i * G::P1,
-                                     halo);
+            c_ingredients<L, LH, BY, BX>(P, C, cst + b * G::P1, pst + b * G::P1, pm, p0, pp,
+                                         sing + slot_i * G::P1, halo);
     };
 
     static_assert(L::D == 3, "2-D domains march through the D2Q9R view");
@@ -742,11 +752,11 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
             fetch_ring(z + 2);
         }
         cp_async_commit();
-        if (active_xy) pull_load<L, SP, IS_PHI, WALLS, I>(K, fin, c_n, x, y, z, inside1 && z >= 1 && z + 1 < P.nz, st);
+        if (active_xy) pull_load<LP, SP, IS_PHI, WALLS, I>(K, fin, c_n, x, y, z, inside1 && z >= 1 && z + 1 < P.nz, st);
         ingredients(islot(z + 1), fslot(z), fslot(z + 1), fslot(z + 2), z + 1);
         __syncthreads();
         if (active_xy)
-            pull_combine<L, SP, BY, BX, IS_PHI, WALLS, I>(K, C, fout, sing + islot(z - 1) * G::P1,
+            pull_combine<LP, SP, BY, BX, IS_PHI, WALLS, I>(K, C, fout, sing + islot(z - 1) * G::P1,
                                                    sing + islot(z) * G::P1, sing + islot(z + 1) * G::P1,
                                                    fslot(z - 1), fslot(z), fslot(z + 1), sA + islot(z) * G::P1,
                                                    phi_np1, moment_out, st, macc);
@@ -774,23 +784,24 @@ k_phi_step(const KParams K, const typename SP::store_t* __restrict__ gin,
                                        blockIdx.x * BX, blockIdx.y * BY, blockIdx.z * ZCH, 0);
 }
 
-template <class L, class SP, int BY, int ZCH, int MINB, bool WALLS, int BX = 32>
+template <class L, class SP, int BY, int ZCH, int MINB, bool WALLS, int BX = 32, class LH = L>
 __global__ void __launch_bounds__(BX * BY, MINB)
 k_c_step(const KParams K, const typename SP::store_t* __restrict__ hin,
          typename SP::store_t* __restrict__ hout, const typename SP::real* __restrict__ phi_n,
          const typename SP::real* __restrict__ phi_np1, const typename SP::real* __restrict__ c_n,
          typename SP::real* __restrict__ c_np1, double* __restrict__ mass_partials) {
-    march<L, SP, BY, ZCH, false, WALLS, BX>(K, hin, hout, phi_n, phi_np1, c_n, c_np1, mass_partials,
+    march<L, SP, BY, ZCH, false, WALLS, BX, long long, LH>(K, hin, hout, phi_n, phi_np1, c_n, c_np1, mass_partials,
                                         blockIdx.x * BX, blockIdx.y * BY, blockIdx.z * ZCH,
                                         blockIdx.x + gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z));
 }
 
 // ---- initialisation -------------------------------------------------------------------
 // g_k = w_k phi - G_k/2, h_k = h^eq_k - H_k/2 with H at dphi/dt = 0 (the variable
-// change of Sec. 3.1 applied at equilibrium).  Fields phi, c already hold the
-// start values in the compute type.
+// change of Sec. 3.1 applied at equilibrium), or h_k = h^eq,alt_k with the
+// alternative equilibrium (no H, no shifted variable).  h lives on LH.  Fields
+// phi, c already hold the start values in the compute type.
 
-template <class L, class SP>
+template <class L, class SP, class LH = L>
 __global__ void k_init(const KParams K, const typename SP::real* __restrict__ phi,
                        typename SP::real* __restrict__ c, typename SP::store_t* __restrict__ g,
                        typename SP::store_t* __restrict__ h) {
@@ -822,17 +833,22 @@ __global__ void k_init(const KParams K, const typename SP::real* __restrict__ ph
     const R mu = closure_mu(C, ph, cc);
     const R A = g_isotropic(C, ph, mu);
     const R kct = C.kct * ph * (R(1) - ph) * inv;
-    const R Ps = div36(p_term(C, ph, mu));
+    const R Ps = divw<LH::DEN>(p_term(C, ph, mu));
     const R f = mu * C.Dp;
-    R hsum = R(0), hcomp = R(0);
 #pragma unroll
     for (int k = 0; k < L::Q; ++k) {
         const R wk = R(L::w(k));
         const R Gk = wk * (A + kct * edot<L>(k, gx, gy, gz));
         SP::store(g, (long long)k * P.N + i, wk * ph - R(0.5) * Gk, wk * ph);
-        const R Hk = C.gamma * wk * f * edot<L>(k, gx, gy, gz);
-        const R heq = (k == 0) ? cc - R(36 - L::m(0)) * Ps : R(L::m(k)) * Ps;
-        const R hk = heq - R(0.5) * Hk;
+    }
+    R hsum = R(0), hcomp = R(0);
+#pragma unroll
+    for (int k = 0; k < LH::Q; ++k) {
+        const R wk = R(LH::w(k));
+        const R ek = edot<LH>(k, gx, gy, gz);
+        const R heq = (k == 0) ? cc - R(LH::DEN - LH::m(0)) * Ps : R(LH::m(k)) * Ps;
+        // H_k = gamma w_k e_k.F, or the flux part w_k e_k.F / xi_s^2 of h^eq,alt
+        const R hk = P.h_eq_alt ? heq + R(3) * wk * f * ek : heq - R(0.5) * (C.gamma * wk * f * ek);
         SP::store(h, (long long)k * P.N + i, hk, heq);
         const R t = hsum + hk;              // Fast2Sum: h_0 (the largest) comes first
         hcomp += (hsum - t) + hk;
@@ -864,7 +880,7 @@ __global__ void k_fields_out(const KParams K, const R* __restrict__ phi, const R
 }
 
 // Expand stored populations to FP64 (deviation modes add their references back).
-template <class L, class SP>
+template <class L, class SP, class LH = L>
 __global__ void k_pops_out(const KParams K, const typename SP::real* __restrict__ phi,
                            const typename SP::real* __restrict__ c, const typename SP::store_t* __restrict__ g,
                            const typename SP::store_t* __restrict__ h, double* __restrict__ og,
@@ -875,12 +891,15 @@ __global__ void k_pops_out(const KParams K, const typename SP::real* __restrict_
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= P.N) return;
     const R ph = phi[i], cc = c[i];
-    const R Ps = div36(p_term(C, ph, closure_mu(C, ph, cc)));
+    const R Ps = divw<LH::DEN>(p_term(C, ph, closure_mu(C, ph, cc)));
 #pragma unroll
     for (int k = 0; k < L::Q; ++k) {
         const R wk = R(L::w(k));
         if (og) og[(long long)k * P.N + i] = (double)SP::load(g, (long long)k * P.N + i, wk * ph);
-        const R heq = (k == 0) ? cc - R(36 - L::m(0)) * Ps : R(L::m(k)) * Ps;
+    }
+#pragma unroll
+    for (int k = 0; k < LH::Q; ++k) {
+        const R heq = (k == 0) ? cc - R(LH::DEN - LH::m(0)) * Ps : R(LH::m(k)) * Ps;
         if (oh) oh[(long long)k * P.N + i] = (double)SP::load(h, (long long)k * P.N + i, heq);
     }
 }
@@ -1018,7 +1037,7 @@ __global__ void k_mass_corr_apply(const MassCorr* __restrict__ mc, typename SP::
 }
 
 // Exact FP64 population mass: h_k expanded (deviation modes add their references
-// back), summed per node in float-float, per block in FP64.
+// back), summed per node in float-float, per block in FP64.  L: the h lattice.
 template <class L, class SP>
 __global__ void __launch_bounds__(kMassThreads)
 k_pop_mass(const KParams K, const typename SP::real* __restrict__ phi, const typename SP::real* __restrict__ c,
@@ -1030,10 +1049,10 @@ k_pop_mass(const KParams K, const typename SP::real* __restrict__ phi, const typ
     for (long long i = blockIdx.x * (long long)kMassThreads + threadIdx.x; i < P.N;
          i += (long long)gridDim.x * kMassThreads) {
         const R ph = phi[i], cc = c[i];
-        const R Ps = div36(p_term(C, ph, closure_mu(C, ph, cc)));
+        const R Ps = divw<L::DEN>(p_term(C, ph, closure_mu(C, ph, cc)));
 #pragma unroll
         for (int k = 0; k < L::Q; ++k) {
-            const R ref = (k == 0) ? cc - R(36 - L::m(0)) * Ps : R(L::m(k)) * Ps;
+            const R ref = (k == 0) ? cc - R(L::DEN - L::m(0)) * Ps : R(L::m(k)) * Ps;
             acc.add(SP::load(h, (long long)k * P.N + i, ref), R(0));
         }
     }

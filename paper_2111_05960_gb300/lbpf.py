@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libgb_lbpf.so")
 LBPF_OK, LBPF_EINVAL, LBPF_ENOMEM, LBPF_ECUDA, LBPF_EUNSTABLE, LBPF_ETIMEOUT, LBPF_ESTATE, \
     LBPF_EUNSUPPORTED = range(8)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EUNSTABLE", "ETIMEOUT", "ESTATE", "EUNSUPPORTED"]
-LBPF_D2Q9, LBPF_D3Q19 = 0, 1
+LBPF_D2Q9, LBPF_D3Q19, LBPF_D2Q5, LBPF_D3Q7 = 0, 1, 2, 3
 LBPF_FP64, LBPF_FP32, LBPF_FP32_BF16DEV, LBPF_FP32_FP16DEV = 0, 1, 2, 3
 PRECISIONS = {"fp64": LBPF_FP64, "fp32": LBPF_FP32, "bf16dev": LBPF_FP32_BF16DEV,
               "fp16dev": LBPF_FP32_FP16DEV}
@@ -43,7 +43,8 @@ class lbpf_params(ctypes.Structure):
                 ("mu_eq", ctypes.c_double), ("counter_term", ctypes.c_int32),
                 ("anti_trapping", ctypes.c_int32), ("a_at", ctypes.c_double),
                 ("eps_n", ctypes.c_double), ("mass_every", ctypes.c_int32),
-                ("checkpoint_every", ctypes.c_int32)]
+                ("checkpoint_every", ctypes.c_int32), ("h_lattice", ctypes.c_int32),
+                ("h_eq_alt", ctypes.c_int32)]
 
 
 _lib = None
@@ -285,6 +286,8 @@ def params_from(model, precision="fp64", dx=1.0, dt=1.0, mass_every=0, checkpoin
     p.a_at, p.eps_n = model.a_at, model.eps_n
     p.mass_every = int(mass_every)
     p.checkpoint_every = int(checkpoint_every)
+    p.h_lattice = int(getattr(model, "h_lattice", 0))
+    p.h_eq_alt = int(getattr(model, "h_eq_alt", 0))
     return p
 
 
@@ -304,6 +307,7 @@ class Simulation:
             c0 = np.ascontiguousarray(c0, dtype=np.float64)
         self.ctx = lbpf_create(self.params, phi0, c0, int(is_dev), stream)
         self.q = 19 if self.params.lattice == LBPF_D3Q19 else 9
+        self.q_h = (7 if self.q == 19 else 5) if self.params.h_lattice else self.q
         self.shape = (model.nz, model.ny, model.nx)
 
     def step(self, n=1):
@@ -334,7 +338,7 @@ class Simulation:
 
     def populations(self):
         g = np.empty((self.q,) + self.shape)
-        h = np.empty((self.q,) + self.shape)
+        h = np.empty((self.q_h,) + self.shape)
         lbpf_get_populations(self.ctx, g, h, 0)
         return g, h
 

@@ -57,9 +57,9 @@ def test_param_struct_layout_matches_header(tmp_path):
 
 
 def test_lattice_info_matches_oracle_and_paper(lib):
-    for lat, dim in ((L.LBPF_D2Q9, 2), (L.LBPF_D3Q19, 3)):
+    for lat, code in ((L.LBPF_D2Q9, 2), (L.LBPF_D3Q19, 3), (L.LBPF_D2Q5, 5), (L.LBPF_D3Q7, 7)):
         e, w = L.lbpf_lattice_info(lat)
-        eo, wo, _ = O.lattice_tables(dim)
+        eo, wo, _ = O.lattice_tables(code)
         assert np.array_equal(e, eo)
         assert np.array_equal(w, wo)
     with pytest.raises(L.LbpfError) as ei:
@@ -77,6 +77,9 @@ def test_default_params(lib):
     (lambda p: setattr(p, "nx", 0), "grid sizes"),
     (lambda p: setattr(p, "nz", 4), "D2Q9 needs nz"),
     (lambda p: setattr(p, "lattice", 5), "unknown lattice"),
+    (lambda p: setattr(p, "lattice", L.LBPF_D2Q5), "unknown lattice"),
+    (lambda p: setattr(p, "h_lattice", 2), "h_lattice must be 0 or 1"),
+    (lambda p: setattr(p, "h_eq_alt", -1), "h_eq_alt must be 0 or 1"),
     (lambda p: setattr(p, "precision", 9), "unknown precision"),
     (lambda p: setattr(p, "tau_g", 0.0), "tau_g"),
     (lambda p: setattr(p, "W", -1.0), "W must be"),
@@ -152,3 +155,29 @@ def test_adjoint_arguments_are_checked_on_the_host(lib):
     with pytest.raises(L.LbpfError) as ei:
         L.lbpf_create_batch([good, bad], [a, a], [a, a])
     assert ei.value.status == L.LBPF_EUNSUPPORTED
+
+
+def test_h_variants_rejected_where_not_built(lib):
+    """The adjoint and the batches cover the main composition scheme only: h on
+    the small lattice or with h^eq,alt is refused with EUNSUPPORTED before any
+    device work."""
+    a = np.zeros(64 * 64)
+    for field in ("h_lattice", "h_eq_alt"):
+        p = L.lbpf_default_params()
+        setattr(p, field, 1)
+        p.checkpoint_every = 10
+        with pytest.raises(L.LbpfError) as ei:
+            L.lbpf_create(p, a, a, 0)
+        assert ei.value.status == L.LBPF_EUNSUPPORTED
+        p.checkpoint_every = 0
+        with pytest.raises(L.LbpfError) as ei:
+            L.lbpf_create_batch([L.lbpf_default_params(), p], [a, a], [a, a])
+        assert ei.value.status == L.LBPF_EUNSUPPORTED
+        assert "instance" in str(ei.value) or "batches" in str(ei.value)
+
+
+def test_params_from_carries_the_h_variants(lib):
+    m = WL.recipe(40, 30, D_l=0.1, D_s=0.0, W=2.0)
+    m.h_lattice, m.h_eq_alt = 1, 1
+    p = L.params_from(m, "fp32")
+    assert (p.h_lattice, p.h_eq_alt) == (1, 1)
