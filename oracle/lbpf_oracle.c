@@ -47,6 +47,21 @@
  *     for D2Q9 (tau_h = 3 dt / (gamma dx^2) unchanged): D2Q5 w = 1/3, 1/6;
  *     D3Q7 w = 0, 1/6.  g, the gradient and the normal keep D2Q9 / D3Q19.
  *
+ * Unequal curvatures of the two parabolas (unequal_eps = 1, eps_ratio =
+ * eps_s / eps_l, Sec. 2.3): with e_s = sqrt(eps_s / eps_l), e_l = 1 / e_s,
+ *   closure (Eq. Closure, h = phi):
+ *        mu = [c - phi m_l - (1 - phi) m_s] / [e_s phi + e_l (1 - phi)]
+ *   S_phi (Eq. SourceTerm):
+ *        S = p'(phi) [(e_l - e_s) mu^2 / 2 - (m_l - m_s) mu - df]
+ *   anti-trapping (Eq. Anti-Trapping_Quadratic, coefficient a):
+ *        j_at = a W [(e_l - e_s) mu + m_s - m_l] dphi n
+ * The parameters stay the coexistence compositions and mu_eq; m_l, m_s and
+ * df (Delta f^min) follow from the two equilibrium conditions of Sec. 2.3.2
+ * (equal mu at c_s^co and c_l^co, equal grand potentials at mu_eq):
+ *        m_l = c_l^co - e_s mu_eq,  m_s = c_s^co - e_l mu_eq,
+ *        df = (e_l - e_s) mu_eq^2 / 2 - (m_l - m_s) mu_eq.
+ * With eps_s = eps_l these reduce to the closure and sources above.
+ *
  * Lattices: D2Q9 in the paper's ordering (Sec. 3.1); D3Q19 for the 3-D
  * workloads (the paper names D3Q19 among the lattices of its code, Sec. 3.1),
  * with the same directional-derivative gradient over its 18 links.
@@ -80,6 +95,8 @@ typedef struct {
     double eps_n;           /* regularisation of |grad phi| in n */
     int h_lattice;          /* 0: h on the g lattice; 1: D2Q5 / D3Q7 */
     int h_eq_alt;           /* 1: h^eq,alt with H = 0 (Eq. Seq_Concent_Alt) */
+    int unequal_eps;        /* 1: parabolas of curvatures eps_s != eps_l */
+    double eps_ratio;       /* eps_s / eps_l when unequal_eps = 1 */
 } or_params;
 
 /* ---- lattices ---------------------------------------------------------- */
@@ -206,8 +223,26 @@ static long upstream_index(const or_params *p, const lattice *L, int k, int x, i
 
 /* ---- pointwise model functions (Tab. 2 and Sec. 2.3) ------------------ */
 
+/* Parabolas of unequal curvature: e_s, e_l, the minima m_s, m_l and df. */
+typedef struct { double e_s, e_l, m_s, m_l, df; } parabolas;
+
+static parabolas get_parabolas(const or_params *p)
+{
+    parabolas q;
+    q.e_s = sqrt(p->eps_ratio);
+    q.e_l = 1.0 / q.e_s;
+    q.m_l = p->c_l_co - q.e_s * p->mu_eq;
+    q.m_s = p->c_s_co - q.e_l * p->mu_eq;
+    q.df = 0.5 * (q.e_l - q.e_s) * p->mu_eq * p->mu_eq - (q.m_l - q.m_s) * p->mu_eq;
+    return q;
+}
+
 static double closure_mu(const or_params *p, double phi, double c)
 {
+    if (p->unequal_eps) {
+        parabolas q = get_parabolas(p);
+        return (c - phi * q.m_l - (1.0 - phi) * q.m_s) / (q.e_s * phi + q.e_l * (1.0 - phi));
+    }
     /* h(phi) = phi, c^co(phi) = c_l^co h + c_s^co (1 - h) */
     double cco = p->c_l_co * phi + p->c_s_co * (1.0 - phi);
     return p->mu_eq + c - cco;
@@ -216,6 +251,10 @@ static double closure_mu(const or_params *p, double phi, double c)
 static double source_S(const or_params *p, double phi, double mu)
 {
     double pprime = 6.0 * phi * (1.0 - phi);
+    if (p->unequal_eps) {
+        parabolas q = get_parabolas(p);
+        return pprime * (0.5 * (q.e_l - q.e_s) * mu * mu - (q.m_l - q.m_s) * mu - q.df);
+    }
     return pprime * (p->c_s_co - p->c_l_co) * (mu - p->mu_eq);
 }
 
@@ -241,7 +280,12 @@ static void flux_F(const or_params *p, double mu, double dphi,
                    const double grad[3], const double nvec[3], double F[3])
 {
     double Dprime = p->D_l - p->D_s;
-    double at = p->anti_trapping ? p->a_at * p->W * (p->c_s_co - p->c_l_co) * dphi : 0.0;
+    double jump = p->c_s_co - p->c_l_co;
+    if (p->unequal_eps) {
+        parabolas q = get_parabolas(p);
+        jump = (q.e_l - q.e_s) * mu + q.m_s - q.m_l;
+    }
+    double at = p->anti_trapping ? p->a_at * p->W * jump * dphi : 0.0;
     for (int a = 0; a < 3; ++a) F[a] = mu * Dprime * grad[a] + at * nvec[a];
 }
 
@@ -621,7 +665,7 @@ static void finish_adjoint(const or_params *p, const lattice *L, const double *g
 int or_step_adjoint(const or_params *p, const double *g, const double *h, const double *phi, const double *c,
                     double *gb, double *hb, double *phib, double *cb, double *pb)
 {
-    if (p->h_lattice || p->h_eq_alt) return -2;   /* the adjoint covers the main scheme only */
+    if (p->h_lattice || p->h_eq_alt || p->unequal_eps) return -2;   /* the adjoint covers the main scheme only */
     lattice L = get_lattice(p->dim);
     long N = (long)p->nx * p->ny * p->nz;
     int q = L.q;
@@ -730,7 +774,7 @@ int or_step_adjoint(const or_params *p, const double *g, const double *h, const 
 int or_init_adjoint(const or_params *p, const double *phi0, const double *c0, const double *gb, const double *hb,
                     double *phib, double *cb, double *pb)
 {
-    if (p->h_lattice || p->h_eq_alt) return -2;
+    if (p->h_lattice || p->h_eq_alt || p->unequal_eps) return -2;
     lattice L = get_lattice(p->dim);
     long N = (long)p->nx * p->ny * p->nz;
     int q = L.q;

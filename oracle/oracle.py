@@ -84,7 +84,8 @@ class _CParams(ctypes.Structure):
                 ("c_s_co", ctypes.c_double), ("c_l_co", ctypes.c_double),
                 ("mu_eq", ctypes.c_double), ("counter_term", ctypes.c_int),
                 ("anti_trapping", ctypes.c_int), ("a_at", ctypes.c_double),
-                ("eps_n", ctypes.c_double), ("h_lattice", ctypes.c_int), ("h_eq_alt", ctypes.c_int)]
+                ("eps_n", ctypes.c_double), ("h_lattice", ctypes.c_int), ("h_eq_alt", ctypes.c_int),
+                ("unequal_eps", ctypes.c_int), ("eps_ratio", ctypes.c_double)]
 
 
 @dataclass
@@ -93,7 +94,9 @@ class OracleParams:
 
     M_phi = tau_g / 3 (Sec. 3.2) and gamma = 3 / tau_h (Sec. 3.3).  h_lattice = 1
     puts h on D2Q5 / D3Q7 (xi_s^2 = 1/3); h_eq_alt = 1 uses the alternative
-    equilibrium of Eq. Seq_Concent_Alt with H = 0 (Sec. 3.3)."""
+    equilibrium of Eq. Seq_Concent_Alt with H = 0 (Sec. 3.3).  unequal_eps = 1
+    gives the parabolas the curvature ratio eps_ratio = eps_s / eps_l (Sec. 2.3:
+    Eq. Closure, Eq. SourceTerm, Eq. Anti-Trapping_Quadratic)."""
     nx: int
     ny: int
     nz: int = 1
@@ -113,6 +116,8 @@ class OracleParams:
     eps_n: float = 1e-12
     h_lattice: int = 0
     h_eq_alt: int = 0
+    unequal_eps: int = 0
+    eps_ratio: float = 1.0
 
     @property
     def dim(self) -> int:
@@ -143,6 +148,7 @@ class OracleParams:
         c.counter_term, c.anti_trapping = int(self.counter_term), int(self.anti_trapping)
         c.a_at, c.eps_n = self.a_at, self.eps_n
         c.h_lattice, c.h_eq_alt = int(self.h_lattice), int(self.h_eq_alt)
+        c.unequal_eps, c.eps_ratio = int(self.unequal_eps), float(self.eps_ratio)
         return c
 
 
@@ -156,7 +162,8 @@ class _CParamsCS(ctypes.Structure):
                 ("c_s_co", ctypes.c_double * 2), ("c_l_co", ctypes.c_double * 2),
                 ("mu_eq", ctypes.c_double * 2), ("counter_term", ctypes.c_int),
                 ("anti_trapping", ctypes.c_int), ("a_at", ctypes.c_double * 2),
-                ("eps_n", ctypes.c_double * 2), ("h_lattice", ctypes.c_int), ("h_eq_alt", ctypes.c_int)]
+                ("eps_n", ctypes.c_double * 2), ("h_lattice", ctypes.c_int), ("h_eq_alt", ctypes.c_int),
+                ("unequal_eps", ctypes.c_int), ("pad2", ctypes.c_int), ("eps_ratio", ctypes.c_double * 2)]
 
 
 def _dp(a: np.ndarray):
@@ -360,6 +367,8 @@ def _cs_params(p: OracleParams, dparams, h):
         getattr(c, name)[1] = h * d.get(name, 0.0)
     c.counter_term, c.anti_trapping = int(p.counter_term), int(p.anti_trapping)
     c.h_lattice, c.h_eq_alt = int(p.h_lattice), int(p.h_eq_alt)
+    c.unequal_eps = int(p.unequal_eps)
+    c.eps_ratio[0] = p.eps_ratio
     return c
 
 

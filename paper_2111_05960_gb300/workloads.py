@@ -60,6 +60,8 @@ class ModelParams:
     eps_n: float = 1e-12
     h_lattice: int = 0             # 1: h on D2Q5 / D3Q7 (Sec. 3.1)
     h_eq_alt: int = 0              # 1: alternative equilibrium with H = 0 (Sec. 3.3)
+    unequal_eps: int = 0           # 1: parabolas of curvature ratio eps_ratio (Sec. 2.3)
+    eps_ratio: float = 1.0         # eps_s / eps_l
 
     @property
     def shape(self):

@@ -1,0 +1,129 @@
+"""Pins of the oracle's unequal-curvature model (Sec. 2.3: parabolas of
+curvatures eps_s != eps_l; Eq. Closure, Eq. SourceTerm, Eq. Anti-Trapping_Quadratic),
+with e_s = sqrt(eps_s / eps_l), e_l = 1 / e_s and the parabola minima m_s, m_l and
+Delta f^min fixed by the two equilibrium conditions of Sec. 2.3.2 at the given
+coexistence compositions and mu_eq.
+
+In a bulk phase the closure makes c = m_l + e_s mu (liquid) or m_s + e_l mu
+(solid), so the mixed formulation dc/dt = div(D grad mu) is diffusion of c with
+D_l / e_s (liquid) and D_s / e_l (solid): the pins below use that, the
+equilibrium state, exact conservation and the one-sided Stefan solution with the
+liquid diffusivity D_l / e_s.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy.special import erfc
+
+import oracle as O
+from paper_2111_05960_gb300 import workloads as WL
+
+
+def _minima(rho, c_s=0.6, c_l=0.5, mu_eq=0.4):
+    e_s = math.sqrt(rho)
+    return e_s, 1.0 / e_s, c_l - e_s * mu_eq, c_s - mu_eq / e_s
+
+
+@pytest.mark.parametrize("rho", [0.5, 2.0])
+def test_equilibrium_front_is_stationary(rho):
+    """At mu = mu_eq both parabolas give their coexistence compositions, so the
+    tanh front with c = c^co(phi) has mu = mu_eq everywhere and S_phi = 0
+    (equal grand potentials).  Catches a wrong closure factor, wrong minima or a
+    wrong Delta f^min (S_phi != 0 moves the front)."""
+    nx, W = 96, 4.0
+    # D_s = D_l: with D' != 0 the discrete laplacian of D mu and the finite-difference
+    # div(mu D' grad phi) do not cancel for a uniform mu != 0, which moves even the
+    # equal-curvature front by ~0.1 cell over these steps
+    p = O.OracleParams(nx=nx, ny=4, bc=(1, 0, 0), tau_g=0.36, tau_h=0.36, W=W, lam=30.0, D_l=0.1,
+                       D_s=0.1, c_s_co=0.6, c_l_co=0.5, mu_eq=0.4, counter_term=1, anti_trapping=0,
+                       unequal_eps=1, eps_ratio=rho)
+    x = np.arange(nx, dtype=float)
+    phi0 = np.tile(WL.tanh_profile(x - 47.5, W), (4, 1))[None]
+    c0 = WL.blend(phi0, 0.6, 0.5)
+    o = O.Oracle(p, phi0, c0)
+    assert np.abs(o.mu - 0.4).max() < 1e-14
+    pos = lambda ph: (1 - ph[0].mean(0)).sum()
+    o.step(200)
+    x1 = pos(o.phi)
+    o.step(2000)
+    assert abs(pos(o.phi) - x1) < 0.05
+    assert abs(x1 - pos(phi0)) < 0.05
+    assert np.abs(o.mu - 0.4).max() < 1e-4
+
+
+@pytest.mark.parametrize("rho,phase", [(2.0, "liquid"), (0.5, "liquid"), (2.0, "solid"), (0.5, "solid")])
+def test_bulk_diffusivity_follows_the_closure(rho, phase):
+    """A Fourier mode of c decays at (D_l / e_s) k^2 in the liquid and (D_s / e_l) k^2
+    in the solid.  Catches e_s and e_l exchanged or a closure factor dropped."""
+    L = 48
+    k = 2 * math.pi / L
+    y, x = np.mgrid[0:L, 0:L].astype(float)
+    mode = np.sin(k * x)
+    D_l, D_s = 0.1, 0.06
+    p = O.OracleParams(nx=L, ny=L, tau_g=0.36, tau_h=0.9, W=3.0, lam=5.0, D_l=D_l, D_s=D_s,
+                       counter_term=1, anti_trapping=1, unequal_eps=1, eps_ratio=rho)
+    phi = 1.0 if phase == "liquid" else 0.0
+    o = O.Oracle(p, np.full((1, L, L), phi), 0.5 + 0.05 * mode[None])
+    n = 800
+    o.step(n)
+    amp = float(((o.c[0] - 0.5) * mode).sum() / (mode * mode).sum())
+    e_s, e_l, _, _ = _minima(rho)
+    D = D_l / e_s if phase == "liquid" else D_s / e_l
+    assert -math.log(amp / 0.05) / n == pytest.approx(D * k * k, rel=0.02)
+
+
+def test_equal_curvatures_reduce_to_the_main_model():
+    """eps_s = eps_l through the general formulas gives the main model's state
+    (the two differ by rounding only)."""
+    phi0, c0 = WL.random_fields((1, 14, 18), seed=9)
+    out = []
+    for flag in (0, 1):
+        p = O.OracleParams(nx=18, ny=14, bc=(1, 0, 0), tau_g=0.7, tau_h=0.9, lam=4.0, D_l=0.15,
+                           D_s=0.03, anti_trapping=1, unequal_eps=flag, eps_ratio=1.0)
+        out.append(O.Oracle(p, phi0, c0).step(200))
+    for a in ("phi", "c"):
+        ref = getattr(out[0], a)
+        assert np.abs(getattr(out[1], a) - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("dim,bc", [(2, (0, 0, 0)), (2, (1, 1, 0)), (3, (1, 0, 1))])
+def test_solute_mass_is_conserved(dim, bc):
+    shape = (6 if dim == 3 else 1, 10, 12)
+    phi0, c0 = WL.random_fields(shape, seed=31 + dim)
+    p = O.OracleParams(nx=12, ny=10, nz=shape[0], bc=bc, tau_g=0.7, tau_h=0.9, lam=4.0, D_l=0.15,
+                       D_s=0.03, anti_trapping=1, unequal_eps=1, eps_ratio=3.0)
+    o = O.Oracle(p, phi0, c0)
+    m0 = o.c.sum()
+    o.step(200)
+    assert abs(o.c.sum() - m0) / m0 < 1e-13
+    assert np.all(np.isfinite(o.phi))
+
+
+@pytest.mark.parametrize("rho", [0.5, 2.0, 4.0])
+def test_one_sided_stefan_dissolution_unequal_curvatures(rho):
+    """Sec. 4.2 scaled to W = 10 (D_s = 0, j_at, lambda* = 230) with eps_s / eps_l = rho.
+    In the liquid c = m_l + e_s mu diffuses with D_l / e_s, so the sharp-interface
+    front is x_i = 2 alpha sqrt(D_l t / e_s) with alpha the root of
+    Eq. Cartesian_Transcendental for (c_l^co - c_inf) / (dc sqrt(pi)), and mu follows
+    the erfc profile of Eq. Analytical_muL_Ds0 with that diffusivity."""
+    nx, ny, n = 1000, 4, 6000
+    p = O.OracleParams(nx=nx, ny=ny, bc=(1, 0, 0), tau_g=1.8, tau_h=1.8, W=10.0, lam=230.0, D_l=0.5,
+                       D_s=0.0, c_s_co=0.6, c_l_co=0.5, mu_eq=0.4, counter_term=1, anti_trapping=1,
+                       a_at=0.25, unequal_eps=1, eps_ratio=rho)
+    x = np.arange(nx) + 0.5 - nx / 2
+    phi = WL.tanh_profile(x, 10.0)
+    c = 0.5 * (1.0 - 0.2 * np.tanh(2 * x / 10.0))     # solid at c_s^co, liquid c_inf = 0.4
+    o = O.Oracle(p, np.tile(phi, (ny, 1)), np.tile(c, (ny, 1)))
+    o.step(n)
+    e_s, _, m_l, _ = _minima(rho)
+    D = 0.5 / e_s
+    alpha = O.stefan_one_sided_root(0.5, 0.4, 0.1)
+    xi = -500 + (1 - o.phi[0].mean(0)).sum()
+    xa = 2 * alpha * math.sqrt(D * n)
+    assert abs(xi - xa) < 0.05 * abs(xa) + 0.5
+    mu_inf = (0.4 - m_l) / e_s
+    mua = mu_inf + (0.4 - mu_inf) * erfc(x / (2 * math.sqrt(D * n))) / erfc(alpha)
+    sel = (x > xi + 20) & (x < 300)
+    mu = o.mu[0].mean(0)
+    assert np.linalg.norm(mu[sel] - mua[sel]) / np.linalg.norm(mua[sel]) < 1.6e-3
