@@ -22,7 +22,9 @@
  * Two variants of the composition scheme named in Sec. 3 are selectable: the
  * alternative equilibrium h^eq,alt that carries the flux with H_k = 0
  * (Eq. LBE_Concent_Alt, Eq. Seq_Concent_Alt), and h on the small lattice of the
- * paper's code (D2Q5 / D3Q7, Sec. 3.1) while g keeps D2Q9 / D3Q19.
+ * paper's code (D2Q5 / D3Q7, Sec. 3.1) while g keeps D2Q9 / D3Q19.  The
+ * free energies may also be parabolas of unequal curvature (Sec. 2.3:
+ * Eq. Closure, Eq. SourceTerm, Eq. Anti-Trapping_Quadratic).
  *
  * Conventions shared by every entry point:
  *   - Every call returns an lbpf_status and never throws across the ABI.
@@ -115,6 +117,17 @@ typedef struct {
                                     equilibrium h^eq,alt_k = w_k [gamma D mu + e_k.F /
                                     xi_s^2] with H_k = 0 (Eq. Seq_Concent_Alt), F = mu D'
                                     grad phi + j_at */
+    int32_t unequal_eps;         /* 0: parabolas of equal curvature (the closure and
+                                    sources above); 1: curvature ratio eps_ratio, with
+                                    e_s = sqrt(eps_ratio), e_l = 1/e_s:
+                                      mu = [c - m_l phi - m_s (1-phi)] / [e_s phi + e_l (1-phi)]
+                                      S_phi = p'(phi) [(e_l-e_s) mu^2/2 - (m_l-m_s) mu - df]
+                                      j_at = a W [(e_l-e_s) mu + m_s - m_l] dphi/dt n
+                                    where m_l = c_l^co - e_s mu_eq, m_s = c_s^co - e_l mu_eq
+                                    and df = (e_l-e_s) mu_eq^2/2 - (m_l-m_s) mu_eq (equal
+                                    chemical potentials at c_s^co, c_l^co and equal grand
+                                    potentials at mu_eq, Sec. 2.3.2) */
+    double eps_ratio;            /* eps_s / eps_l (> 0) when unequal_eps = 1 */
 } lbpf_params;
 
 typedef struct lbpf_ctx lbpf_ctx;
@@ -122,7 +135,8 @@ typedef struct lbpf_ctx lbpf_ctx;
 /* Fill *p with defaults: 2-D D2Q9 64x64 periodic, FP64, dx = dt = 1,
  * tau_g = tau_h = 0.36, W = 3, lambda = 0, D_l = D_s = 0.1, c_s^co = 1,
  * c_l^co = 0.5, mu_eq = 0.4, counter term on, anti-trapping off, a = -1 (auto),
- * eps_n = 1e-12, h on the lattice of g with H_k (h_lattice = h_eq_alt = 0).
+ * eps_n = 1e-12, h on the lattice of g with H_k (h_lattice = h_eq_alt = 0),
+ * equal curvatures (unequal_eps = 0, eps_ratio = 1).
  * Returns LBPF_EINVAL if p is NULL. */
 lbpf_status lbpf_default_params(lbpf_params *p);
 
@@ -136,9 +150,9 @@ lbpf_status lbpf_default_params(lbpf_params *p);
  * everything; on failure *out is NULL and nothing is leaked.
  * Errors: EINVAL (NULL pointers, sizes < 1, nz != 1 for D2Q9, a bounce-back
  * axis with fewer than 2 nodes, tau <= 0, W <= 0, D < 0, unknown enum,
- * h_lattice or h_eq_alt not 0 / 1), ENOMEM, ECUDA, EUNSUPPORTED
- * (checkpoint_every > 0 with h_lattice = 1 or h_eq_alt = 1: the adjoint covers
- * the main scheme only). */
+ * h_lattice, h_eq_alt or unequal_eps not 0 / 1, eps_ratio <= 0), ENOMEM,
+ * ECUDA, EUNSUPPORTED (checkpoint_every > 0 with h_lattice, h_eq_alt or
+ * unequal_eps set: the adjoint covers the main scheme only). */
 lbpf_status lbpf_create(const lbpf_params *p, const double *phi0, const double *c0,
                         int32_t ptr_is_device, void *cuda_stream, lbpf_ctx **out);
 
@@ -214,7 +228,8 @@ lbpf_status lbpf_lattice_info(int32_t lattice, int32_t *q, int32_t *e, double *w
  * all instances, so the work is balanced whatever the size mix.  p[i], phi0[i],
  * c0[i] describe instance i exactly as for lbpf_create (each with its own
  * sizes, walls and parameters); all instances must be D2Q9 with the same
- * precision, mass_every = 0, checkpoint_every = 0, h_lattice = h_eq_alt = 0
+ * precision, mass_every = 0, checkpoint_every = 0, h_lattice = h_eq_alt =
+ * unequal_eps = 0
  * and 9 nx ny x (bytes per
  * stored value: 8 FP64, 4 FP32, 2 for 16-bit storage) < 2^31 (the kernels
  * address within an instance with 32-bit byte offsets).  The fields are copied;
@@ -224,7 +239,8 @@ lbpf_status lbpf_lattice_info(int32_t lattice, int32_t *q, int32_t *e, double *w
  * LBPF_EUNSUPPORTED (use the calls below).
  * Errors: EINVAL (NULL pointers, n < 1, an invalid or oversized instance: the
  * message names it), EUNSUPPORTED (non-D2Q9 instance, mass_every != 0,
- * checkpoint_every != 0, h_lattice != 0, h_eq_alt != 0), ENOMEM, ECUDA. */
+ * checkpoint_every != 0, h_lattice, h_eq_alt or unequal_eps != 0), ENOMEM,
+ * ECUDA. */
 lbpf_status lbpf_create_batch(const lbpf_params *p, int32_t n, const double *const *phi0,
                               const double *const *c0, int32_t ptr_is_device, void *cuda_stream,
                               lbpf_ctx **out);

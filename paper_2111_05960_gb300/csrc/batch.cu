@@ -216,8 +216,8 @@ lbpf_status lbpf_create_batch(const lbpf_params* p, int32_t n, const double* con
         if (p[i].precision != p[0].precision) return fail(nullptr, LBPF_EINVAL, "all instances need one precision");
         if (p[i].mass_every != 0) return fail(nullptr, LBPF_EUNSUPPORTED, "mass correction is not built for batches");
         if (p[i].checkpoint_every != 0) return fail(nullptr, LBPF_EUNSUPPORTED, "the adjoint is not built for batches");
-        if (p[i].h_lattice != 0 || p[i].h_eq_alt != 0)
-            return fail(nullptr, LBPF_EUNSUPPORTED, "batches keep h on D2Q9 with H_k");
+        if (p[i].h_lattice != 0 || p[i].h_eq_alt != 0 || p[i].unequal_eps != 0)
+            return fail(nullptr, LBPF_EUNSUPPORTED, "batches keep h on D2Q9 with H_k and equal curvatures");
     }
     const BatchDispatch* bops = pick_batch(p[0].precision);
     if (!bops) return fail(nullptr, LBPF_EUNSUPPORTED, "precision not built");

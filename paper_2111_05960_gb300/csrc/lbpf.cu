@@ -267,6 +267,8 @@ lbpf_status lbpf_rt::validate(const lbpf_params* p, std::string& why) {
     if (p->checkpoint_every < 0) return bad("checkpoint_every must be >= 0");
     if (p->h_lattice != 0 && p->h_lattice != 1) return bad("h_lattice must be 0 or 1");
     if (p->h_eq_alt != 0 && p->h_eq_alt != 1) return bad("h_eq_alt must be 0 or 1");
+    if (p->unequal_eps != 0 && p->unequal_eps != 1) return bad("unequal_eps must be 0 or 1");
+    if (p->unequal_eps && !(p->eps_ratio > 0 && std::isfinite(p->eps_ratio))) return bad("eps_ratio must be > 0");
     return LBPF_OK;
 }
 
@@ -293,6 +295,14 @@ StepParams lbpf_rt::lattice_units(const lbpf_params* p) {
     s.counter_term = p->counter_term ? 1 : 0;
     s.h_den = p->h_lattice ? 6 : 36;     // w_k = m_k / DEN on the h lattice
     s.h_eq_alt = p->h_eq_alt ? 1 : 0;
+    // parabolas: the minima and Delta f^min from the two equilibrium conditions
+    // (equal mu at the coexistence compositions, equal grand potentials at mu_eq)
+    s.unequal = p->unequal_eps ? 1 : 0;
+    s.e_s = p->unequal_eps ? std::sqrt(p->eps_ratio) : 1.0;
+    s.e_l = 1.0 / s.e_s;
+    s.m_l = s.c_l - s.e_s * s.mu_eq;
+    s.m_s = s.c_s - s.e_l * s.mu_eq;
+    s.df = 0.5 * (s.e_l - s.e_s) * s.mu_eq * s.mu_eq - (s.m_l - s.m_s) * s.mu_eq;
     return s;
 }
 
@@ -487,6 +497,7 @@ lbpf_status lbpf_default_params(lbpf_params* p) {
     p->c_s_co = 1.0; p->c_l_co = 0.5; p->mu_eq = 0.4;
     p->counter_term = 1; p->anti_trapping = 0; p->a_at = -1.0;
     p->eps_n = 1e-12;
+    p->eps_ratio = 1.0;
     return LBPF_OK;
 }
 
@@ -501,8 +512,9 @@ lbpf_status lbpf_create(const lbpf_params* p, const double* phi0, const double* 
     if (!ops) return fail(nullptr, LBPF_EUNSUPPORTED, "lattice/precision not built");
     const AdjDispatch* aops = nullptr;
     if (p->checkpoint_every > 0) {
-        if (p->h_lattice || p->h_eq_alt)
-            return fail(nullptr, LBPF_EUNSUPPORTED, "the adjoint covers h on the lattice of g with H_k only");
+        if (p->h_lattice || p->h_eq_alt || p->unequal_eps)
+            return fail(nullptr, LBPF_EUNSUPPORTED,
+                        "the adjoint covers h on the lattice of g with H_k and equal curvatures only");
         aops = pick_adjoint(p->lattice, p->precision);
         if (!aops) return fail(nullptr, LBPF_EUNSUPPORTED, "the adjoint is built for FP64 and FP32 storage only");
         if (p->ny > 8 * 65535) return fail(nullptr, LBPF_EUNSUPPORTED, "the adjoint needs ny <= 524280");

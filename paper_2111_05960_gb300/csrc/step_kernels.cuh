@@ -54,6 +54,11 @@ struct StepParams {
     int counter_term;
     int h_den;          // DEN of the h lattice: 36 (D2Q9 / D3Q19) or 6 (D2Q5 / D3Q7)
     int h_eq_alt;       // 1: h^eq,alt with H_k = 0 (Eq. Seq_Concent_Alt)
+    // parabolas of unequal curvature (Sec. 2.3): e_s = sqrt(eps_s / eps_l),
+    // e_l = 1 / e_s, minima m_s, m_l and df = Delta f^min from the equilibrium
+    // conditions at c_s^co, c_l^co, mu_eq
+    int unequal;
+    double e_s, e_l, m_s, m_l, df;
 };
 
 // Derived constants of one simulation in the compute type, precomputed on the
@@ -62,9 +67,15 @@ struct StepParams {
 //   G^st = kst S_phi,  kst = -lambda M / W^2;  G^dw = kdw omega',  kdw = -8 M / W^2
 //   counter-term magnitude (4/W) phi (1 - phi) = kct phi (1 - phi)
 //   j_at = atk dphi n,  atk = a W (c_s^co - c_l^co)
+// With unequal curvatures (unequal = 1; Eq. Closure, SourceTerm, Anti-Trapping_Quadratic):
+//   mu = (c - m_l phi - m_s (1 - phi)) / (e_s phi + e_l (1 - phi))
+//   S_phi = 6 phi (1 - phi) [(hq mu - dm) mu - df],  hq = (e_l - e_s)/2, dm = m_l - m_s
+//   j_at = (atk1 mu + atk0) dphi n,  atk1 = a W (e_l - e_s), atk0 = a W (m_s - m_l)
 template <typename R>
 struct Coef {
     R mu_eq, c_l, c_s, kS, kst, kdw, kct, D_l, D_s, Dp, gamma, atk, omg, omh, eps2;
+    int unequal;
+    R e_s, e_l, m_s, m_l, hq, dm, df, atk1, atk0;
     R kct36;   // (1 - w_g/2) kct / 36: the counter-term vector per unit m_k
     // the flux vector of the h collision per unit m_k of the h lattice (w_k =
     // m_k / DEN): (1 - w_h/2) gamma / DEN for H_k (Eq. SourceTerm_LBE_h), or
@@ -86,6 +97,11 @@ __host__ Coef<R> make_coef(const StepParams& P) {
     c.omg = R(P.omg); c.omh = R(P.omh); c.eps2 = R(P.eps2);
     c.kct36 = R((1.0 - 0.5 * P.omg) * (P.counter_term ? 4.0 / P.W : 0.0) / 36.0);
     c.khw = R(P.h_eq_alt ? 3.0 * P.omh / P.h_den : (1.0 - 0.5 * P.omh) * P.gamma / P.h_den);
+    c.unequal = P.unequal;
+    c.e_s = R(P.e_s); c.e_l = R(P.e_l); c.m_s = R(P.m_s); c.m_l = R(P.m_l);
+    c.hq = R(0.5 * (P.e_l - P.e_s)); c.dm = R(P.m_l - P.m_s); c.df = R(P.df);
+    const double aW = P.a_at * P.W;
+    c.atk1 = R(aW * (P.e_l - P.e_s)); c.atk0 = R(aW * (P.m_s - P.m_l));
     return c;
 }
 
@@ -248,14 +264,25 @@ __device__ __forceinline__ R div36(R x) { return divw<36>(x); }
 template <typename R>
 __device__ __forceinline__ R g_isotropic(const Coef<R>& C, R phi, R mu) {
     const R pq = phi * (R(1) - phi);
-    const R S = C.kS * pq * (mu - C.mu_eq);
+    const R S = C.unequal ? R(6) * pq * ((C.hq * mu - C.dm) * mu - C.df)   // Eq. SourceTerm
+                          : C.kS * pq * (mu - C.mu_eq);
     return C.kst * S + C.kdw * (R(2) * pq * (R(1) - R(2) * phi));
 }
 
-// Closure mu = mu_eq + c - c^co(phi) (Eq. PotChim_Equilibirum, h = phi).
+// Closure mu = mu_eq + c - c^co(phi) (Eq. PotChim_Equilibirum, h = phi), or
+// Eq. Closure for parabolas of unequal curvature.
 template <typename R>
 __device__ __forceinline__ R closure_mu(const Coef<R>& C, R phi, R c) {
+    if (C.unequal)
+        return (c - (C.m_l * phi + C.m_s * (R(1) - phi))) / (C.e_s * phi + C.e_l * (R(1) - phi));
     return C.mu_eq + c - (C.c_l * phi + C.c_s * (R(1) - phi));
+}
+
+// Coefficient of dphi n in j_at: a W (c_s^co - c_l^co) (Eq. Anti-trapping_Equilibrium),
+// or a W [(e_l - e_s) mu + m_s - m_l] (Eq. Anti-Trapping_Quadratic).
+template <typename R>
+__device__ __forceinline__ R at_coef(const Coef<R>& C, R mu) {
+    return C.unequal ? C.atk1 * mu + C.atk0 : C.atk;
 }
 
 // P = gamma D(phi) mu with D = D_l phi + D_s (1 - phi) (Sec. 2.3.3).
@@ -455,7 +482,7 @@ __device__ __forceinline__ void c_ingredients(const StepParams& P, const Coef<R>
         R gx, gy, gz_;
         plane_gradient<L, BY, BX>(pm, p0, pp, c2, gx, gy, gz_);
         const R inv = rsqrt_reg<R>(gx * gx + gy * gy + gz_ * gz_, C.eps2);
-        const R f = mu * C.Dp + C.atk * dphi * inv;        // F = (mu D' + j_at / |grad|) grad
+        const R f = mu * C.Dp + at_coef(C, mu) * dphi * inv;   // F = (mu D' + j_at / |grad|) grad
         V4<R> v;
         v.a = divw<LH::DEN>(p_term(C, ph, mu));          // P per unit m_k of the h lattice
         const R ff = C.khw * f;
@@ -876,7 +903,9 @@ __global__ void k_fields_out(const KParams K, const R* __restrict__ phi, const R
     const double ph = (double)phi[i], cc = (double)c[i];
     if (ophi) ophi[i] = ph;
     if (oc) oc[i] = cc;
-    if (omu) omu[i] = P.mu_eq + cc - (P.c_l * ph + P.c_s * (1.0 - ph));
+    if (omu)
+        omu[i] = P.unequal ? (cc - (P.m_l * ph + P.m_s * (1.0 - ph))) / (P.e_s * ph + P.e_l * (1.0 - ph))
+                           : P.mu_eq + cc - (P.c_l * ph + P.c_s * (1.0 - ph));
 }
 
 // Expand stored populations to FP64 (deviation modes add their references back).

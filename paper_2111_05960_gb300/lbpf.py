@@ -44,7 +44,8 @@ class lbpf_params(ctypes.Structure):
                 ("anti_trapping", ctypes.c_int32), ("a_at", ctypes.c_double),
                 ("eps_n", ctypes.c_double), ("mass_every", ctypes.c_int32),
                 ("checkpoint_every", ctypes.c_int32), ("h_lattice", ctypes.c_int32),
-                ("h_eq_alt", ctypes.c_int32)]
+                ("h_eq_alt", ctypes.c_int32), ("unequal_eps", ctypes.c_int32),
+                ("eps_ratio", ctypes.c_double)]
 
 
 _lib = None
@@ -288,6 +289,8 @@ def params_from(model, precision="fp64", dx=1.0, dt=1.0, mass_every=0, checkpoin
     p.checkpoint_every = int(checkpoint_every)
     p.h_lattice = int(getattr(model, "h_lattice", 0))
     p.h_eq_alt = int(getattr(model, "h_eq_alt", 0))
+    p.unequal_eps = int(getattr(model, "unequal_eps", 0))
+    p.eps_ratio = float(getattr(model, "eps_ratio", 1.0))
     return p
 
 

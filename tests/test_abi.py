@@ -71,6 +71,7 @@ def test_default_params(lib):
     p = L.lbpf_default_params()
     assert (p.nx, p.ny, p.nz) == (64, 64, 1)
     assert p.precision == L.LBPF_FP64 and p.counter_term == 1 and p.a_at == -1.0
+    assert (p.h_lattice, p.h_eq_alt, p.unequal_eps, p.eps_ratio) == (0, 0, 0, 1.0)
 
 
 @pytest.mark.parametrize("mutate,msg", [
@@ -80,6 +81,8 @@ def test_default_params(lib):
     (lambda p: setattr(p, "lattice", L.LBPF_D2Q5), "unknown lattice"),
     (lambda p: setattr(p, "h_lattice", 2), "h_lattice must be 0 or 1"),
     (lambda p: setattr(p, "h_eq_alt", -1), "h_eq_alt must be 0 or 1"),
+    (lambda p: setattr(p, "unequal_eps", 3), "unequal_eps must be 0 or 1"),
+    (lambda p: (setattr(p, "unequal_eps", 1), setattr(p, "eps_ratio", 0.0)), "eps_ratio"),
     (lambda p: setattr(p, "precision", 9), "unknown precision"),
     (lambda p: setattr(p, "tau_g", 0.0), "tau_g"),
     (lambda p: setattr(p, "W", -1.0), "W must be"),
@@ -162,7 +165,7 @@ def test_h_variants_rejected_where_not_built(lib):
     the small lattice or with h^eq,alt is refused with EUNSUPPORTED before any
     device work."""
     a = np.zeros(64 * 64)
-    for field in ("h_lattice", "h_eq_alt"):
+    for field in ("h_lattice", "h_eq_alt", "unequal_eps"):
         p = L.lbpf_default_params()
         setattr(p, field, 1)
         p.checkpoint_every = 10
