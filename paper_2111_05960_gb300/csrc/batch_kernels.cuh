@@ -67,10 +67,10 @@ k_batch_step(const BatchInst* __restrict__ inst, const int* __restrict__ tile_in
         __syncthreads();
         const typename SP::real* pn1 = phi_np1 ? phi_np1 + fo : nullptr;
         if (walls)
-            march<D2Q9R, SP, 1, ROWS, IS_PHI, true, BX, int>(sK, fin + po, fout + po, phi_n + fo, pn1, c_n + fo,
+            march<D2Q9R, SP, 1, ROWS, IS_PHI, true, BX, int, D2Q9R, false>(sK, fin + po, fout + po, phi_n + fo, pn1, c_n + fo,
                                                         moment_out + fo, nullptr, x0, 0, z0, 0);
         else
-            march<D2Q9R, SP, 1, ROWS, IS_PHI, false, BX, int>(sK, fin + po, fout + po, phi_n + fo, pn1, c_n + fo,
+            march<D2Q9R, SP, 1, ROWS, IS_PHI, false, BX, int, D2Q9R, false>(sK, fin + po, fout + po, phi_n + fo, pn1, c_n + fo,
                                                          moment_out + fo, nullptr, x0, 0, z0, 0);
     }
 }

@@ -261,28 +261,30 @@ __device__ __forceinline__ R div36(R x) { return divw<36>(x); }
 // G^st + G^dw: the isotropic part of G_k / w_k (Eq. SourceG_ST, Eq. SourceG_dw;
 // S_phi of Eq. SourceTerm_Coexistence with p' = 6 phi (1 - phi);
 // omega' = 2 phi (1 - phi)(1 - 2 phi) of Tab. 2).  kdw = 0 with the counter term.
-template <typename R>
+// U = false: equal curvatures known at compile time (the batch kernels, which
+// refuse unequal curvatures, keep their registers for the march).
+template <bool U = true, typename R>
 __device__ __forceinline__ R g_isotropic(const Coef<R>& C, R phi, R mu) {
     const R pq = phi * (R(1) - phi);
-    const R S = C.unequal ? R(6) * pq * ((C.hq * mu - C.dm) * mu - C.df)   // Eq. SourceTerm
-                          : C.kS * pq * (mu - C.mu_eq);
+    const R S = (U && C.unequal) ? R(6) * pq * ((C.hq * mu - C.dm) * mu - C.df)   // Eq. SourceTerm
+                                 : C.kS * pq * (mu - C.mu_eq);
     return C.kst * S + C.kdw * (R(2) * pq * (R(1) - R(2) * phi));
 }
 
 // Closure mu = mu_eq + c - c^co(phi) (Eq. PotChim_Equilibirum, h = phi), or
 // Eq. Closure for parabolas of unequal curvature.
-template <typename R>
+template <bool U = true, typename R>
 __device__ __forceinline__ R closure_mu(const Coef<R>& C, R phi, R c) {
-    if (C.unequal)
+    if (U && C.unequal)
         return (c - (C.m_l * phi + C.m_s * (R(1) - phi))) / (C.e_s * phi + C.e_l * (R(1) - phi));
     return C.mu_eq + c - (C.c_l * phi + C.c_s * (R(1) - phi));
 }
 
 // Coefficient of dphi n in j_at: a W (c_s^co - c_l^co) (Eq. Anti-trapping_Equilibrium),
 // or a W [(e_l - e_s) mu + m_s - m_l] (Eq. Anti-Trapping_Quadratic).
-template <typename R>
+template <bool U = true, typename R>
 __device__ __forceinline__ R at_coef(const Coef<R>& C, R mu) {
-    return C.unequal ? C.atk1 * mu + C.atk0 : C.atk;
+    return (U && C.unequal) ? C.atk1 * mu + C.atk0 : C.atk;
 }
 
 // P = gamma D(phi) mu with D = D_l phi + D_s (1 - phi) (Sec. 2.3.3).
@@ -430,7 +432,7 @@ __device__ __forceinline__ void plane_gradient(const R* pm, const R* p0, const R
 
 // Ingredients of the phi collision on one plane: alpha_g, beta_g (x, y, z) and
 // A = G^st + G^dw.
-template <class L, int BY, int BX, typename R>
+template <class L, int BY, int BX, bool U, typename R>
 __device__ __forceinline__ void phi_ingredients(const StepParams& P, const Coef<R>& C, const R* cst,
                                                 const R* pm, const R* p0, const R* pp, V4<R>* ing, R* sA,
                                                 const HaloOffsets<Geo<L, BY, BX>>& H) {
@@ -444,8 +446,8 @@ __device__ __forceinline__ void phi_ingredients(const StepParams& P, const Coef<
         if (s >= G::P1) break;
         const int c2 = H.c2[it];
         const R ph = p0[c2];
-        const R mu = closure_mu(C, ph, cst[s]);
-        const R A = g_isotropic(C, ph, mu);
+        const R mu = closure_mu<U>(C, ph, cst[s]);
+        const R A = g_isotropic<U>(C, ph, mu);
         V4<R> v;
         v.a = div36(C.omg * ph + half_src * A);         // per unit m_k (w_k = m_k / 36)
         if (P.counter_term) {
@@ -464,7 +466,7 @@ __device__ __forceinline__ void phi_ingredients(const StepParams& P, const Coef<
 
 // Ingredients of the h collision on one plane: P = gamma D mu and
 // beta_h = (1 - w_h/2) gamma (mu D' grad phi + j_at).
-template <class L, class LH, int BY, int BX, typename R>
+template <class L, class LH, int BY, int BX, bool U, typename R>
 __device__ __forceinline__ void c_ingredients(const StepParams& P, const Coef<R>& C, const R* cst, const R* pst,
                                               const R* pm, const R* p0, const R* pp, V4<R>* ing,
                                               const HaloOffsets<Geo<L, BY, BX>>& H) {
@@ -478,11 +480,11 @@ __device__ __forceinline__ void c_ingredients(const StepParams& P, const Coef<R>
         const int c2 = H.c2[it];
         const R ph = p0[c2];
         const R dphi = pst[s] - ph;                        // explicit Euler dphi/dt
-        const R mu = closure_mu(C, ph, cst[s]);
+        const R mu = closure_mu<U>(C, ph, cst[s]);
         R gx, gy, gz_;
         plane_gradient<L, BY, BX>(pm, p0, pp, c2, gx, gy, gz_);
         const R inv = rsqrt_reg<R>(gx * gx + gy * gy + gz_ * gz_, C.eps2);
-        const R f = mu * C.Dp + at_coef(C, mu) * dphi * inv;   // F = (mu D' + j_at / |grad|) grad
+        const R f = mu * C.Dp + at_coef<U>(C, mu) * dphi * inv;   // F = (mu D' + j_at / |grad|) grad
         V4<R> v;
         v.a = divw<LH::DEN>(p_term(C, ph, mu));          // P per unit m_k of the h lattice
         const R ff = C.khw * f;
@@ -577,7 +579,7 @@ __device__ __forceinline__ void pull_load(const KParams& K, const typename SP::s
 // Collision of each pulled population at its upstream node from the ingredient
 // planes im (z-1), i0 (z), ip (z+1) (phi planes fm, f0, fp likewise), the new
 // moment, and the stores.
-template <class L, class SP, int BY, int BX, bool IS_PHI, bool WALLS, typename I>
+template <class L, class SP, int BY, int BX, bool IS_PHI, bool WALLS, typename I, bool U>
 __device__ __forceinline__ void pull_combine(const KParams& K, const Coef<typename SP::real>& C,
                                              typename SP::store_t* __restrict__ fout,
                                              const V4<typename SP::real>* im, const V4<typename SP::real>* i0,
@@ -656,7 +658,7 @@ __device__ __forceinline__ void pull_combine(const KParams& K, const Coef<typena
         moment_out[xi] = sum;                      // Eq. Moment0_LBM_Concent
         if (hold) {
             const R phin = phi_np1_in[xi];
-            const R Ps = divw<L::DEN>(p_term(C, phin, closure_mu(C, phin, sum)));
+            const R Ps = divw<L::DEN>(p_term(C, phin, closure_mu<U>(C, phin, sum)));
             // the mass regulated by the correction is that of the populations as
             // stored (quantised), i.e. of the values the next step loads
             const R ref0 = sum - R(L::DEN - L::m(0)) * Ps;
@@ -697,7 +699,7 @@ __device__ __forceinline__ void block_mass_out(const MassAcc<R>& m, double* __re
 // exact mass of the populations it writes into mass_partials (one FP64 value
 // per block) when that pointer is not null.
 template <class L, class SP, int BY, int ZCH, bool IS_PHI, bool WALLS, int BX = 32, typename I = long long,
-          class LH = L>
+          class LH = L, bool U = true>
 __device__ __forceinline__ void march(const KParams& K, const typename SP::store_t* __restrict__ fin,
                                       typename SP::store_t* __restrict__ fout,
                                       const typename SP::real* __restrict__ phi_n,
@@ -739,11 +741,11 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
     auto ingredients = [&](int slot_i, const R* pm, const R* p0, const R* pp, int zg) {
         const int b = zg & 1;
         if (IS_PHI)
-            phi_ingredients<L, BY, BX>(P, C, cst + b * G::P1, pm, p0, pp, sing + slot_i * G::P1, sA + slot_i * G::P1,
-                                       halo);
+            phi_ingredients<L, BY, BX, U>(P, C, cst + b * G::P1, pm, p0, pp, sing + slot_i * G::P1,
+                                          sA + slot_i * G::P1, halo);
         else
-            c_ingredients<L, LH, BY, BX>(P, C, cst + b * G::P1, pst + b * G::P1, pm, p0, pp,
-                                         sing + slot_i * G::P1, halo);
+            c_ingredients<L, LH, BY, BX, U>(P, C, cst + b * G::P1, pst + b * G::P1, pm, p0, pp,
+                                            sing + slot_i * G::P1, halo);
     };
 
     static_assert(L::D == 3, "2-D domains march through the D2Q9R view");
@@ -783,7 +785,7 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
         ingredients(islot(z + 1), fslot(z), fslot(z + 1), fslot(z + 2), z + 1);
         __syncthreads();
         if (active_xy)
-            pull_combine<LP, SP, BY, BX, IS_PHI, WALLS, I>(K, C, fout, sing + islot(z - 1) * G::P1,
+            pull_combine<LP, SP, BY, BX, IS_PHI, WALLS, I, U>(K, C, fout, sing + islot(z - 1) * G::P1,
                                                    sing + islot(z) * G::P1, sing + islot(z + 1) * G::P1,
                                                    fslot(z - 1), fslot(z), fslot(z + 1), sA + islot(z) * G::P1,
                                                    phi_np1, moment_out, st, macc);
