@@ -376,3 +376,47 @@ def test_anti_trapping_removes_solid_side_overshoot():
     assert res[1]["l2c"] < res[0]["l2c"]
     assert res[1]["l2mu"] < res[0]["l2mu"]
     assert res[1]["over"] < 1e-10 < 1e-3 < res[0]["over"]
+
+
+# ---- the 3-D lattice (R2) beyond invariants ---------------------------------------
+
+def test_diffusion_mode_decay_3d_d3q19_body_diagonal():
+    """Pure liquid on D3Q19: a Fourier mode along the body diagonal (1, 1, 1) decays
+    at D |k|^2 up to a second-order lattice error, i.e. the 3-D composition scheme
+    is isotropic to leading order: the relative error of the rate falls by ~4 from
+    a period of 24 to 48 nodes and is below 3% at 48 (measured 9.8% and 2.8%).
+    Catches wrong D3Q19 weights (1/3, 1/18, 1/36) or links, which leave an O(1)
+    error that does not converge."""
+    D = 0.08
+    errs = []
+    for L in (24, 48):
+        k = 2 * math.pi / L
+        z, y, x = np.meshgrid(np.arange(L), np.arange(L), np.arange(L), indexing="ij")
+        mode = np.sin(k * (x + y + z))
+        p = O.OracleParams(nx=L, ny=L, nz=L, tau_g=0.36, tau_h=0.9, W=3.0, lam=5.0, D_l=D, D_s=0.5 * D,
+                           counter_term=1, anti_trapping=1)
+        o = O.Oracle(p, np.ones((L, L, L)), 0.5 + 0.05 * mode)
+        n = 300
+        o.step(n)
+        amp = float(((o.c - 0.5) * mode).sum() / (mode * mode).sum())
+        errs.append(abs(-math.log(amp / 0.05) / n / (D * 3 * k * k) - 1))
+    assert errs[1] < 0.03
+    assert 3.0 < errs[0] / errs[1] < 5.0, errs
+
+
+def test_one_sided_stefan_dissolution_3d_d3q19():
+    """The one-sided dissolution of Sec. 4.2 (W = 10, D_s = 0, j_at, lambda* = 230) as a
+    planar front on a 1000 x 2 x 2 D3Q19 grid: x_i = 2 alpha sqrt(D_l t) as in 2-D."""
+    nx, ny, nz, n = 1000, 2, 2, 6000
+    p = O.OracleParams(nx=nx, ny=ny, nz=nz, bc=(1, 0, 0), tau_g=1.8, tau_h=1.8, W=10.0, lam=230.0,
+                       D_l=0.5, D_s=0.0, c_s_co=0.6, c_l_co=0.5, mu_eq=0.4, counter_term=1,
+                       anti_trapping=1, a_at=0.25)
+    x = np.arange(nx) + 0.5 - nx / 2
+    phi = WL.tanh_profile(x, 10.0)
+    c = 0.5 * (1.0 - 0.2 * np.tanh(2 * x / 10.0))
+    o = O.Oracle(p, np.broadcast_to(phi, (nz, ny, nx)), np.broadcast_to(c, (nz, ny, nx)))
+    o.step(n)
+    alpha = O.stefan_one_sided_root(0.4, 0.3, 0.1)
+    xi = -500 + (1 - o.phi.mean((0, 1))).sum()
+    xa = 2 * alpha * math.sqrt(0.5 * n)
+    assert abs(xi - xa) < 0.05 * abs(xa) + 0.5
