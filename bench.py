@@ -378,9 +378,50 @@ def cpu_baseline(model, phi0, c0, budget_s=12.0, single_s=3.0):
     O.Oracle.set_threads(1)
     steps1, el1 = timed(single_s)
     O.Oracle.set_threads(threads)
+    try:
+        other = oracle_other_configs()
+    except Exception as ex:   # context only: never sinks the main baseline
+        O.Oracle.set_threads(threads)
+        other = {"error": str(ex)}
     return {"value": nodes * steps / el / 1e6, "unit": "MLUPS", "cores": threads, "kind": "oracle",
             "sample": "%dx%dx%d z-slab of the 256^3 medium, %d FP64 steps, %.1f s" % (p.nx, p.ny, nz, steps, el),
-            "single_core_value": nodes * steps1 / el1 / 1e6, "cpu_model": cpu_model(), "nproc": os.cpu_count()}
+            "single_core_value": nodes * steps1 / el1 / 1e6, "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+            "other_configs": other}
+
+
+def oracle_other_configs(budget_s=1.5):
+    """The oracle, as it stands, on the other workloads, on all host cores and on
+    one: the 512^2 disc (counter term on) and, for the batch sweep, its smallest,
+    median and largest instance (each timed alone, ~budget_s)."""
+    import oracle as O
+    from paper_2111_05960_gb300 import workloads as WL
+    names = O.OracleParams.__dataclass_fields__
+
+    def rate(model, phi0, c0, budget):
+        o = O.Oracle(O.OracleParams(**{k: getattr(model, k) for k in names}), phi0, c0)
+        t = time.perf_counter()
+        o.step(1)
+        steps = max(1, int(budget / max(time.perf_counter() - t, 1e-3)))
+        t = time.perf_counter()
+        o.step(steps)
+        return model.nodes * steps / (time.perf_counter() - t) / 1e6
+
+    threads = O.Oracle.threads()
+    out = {}
+    m, phi0, c0 = WL.disc_2d(n=512, counter_term=1)
+    out["disc_2d_512"] = {"mlups": rate(m, phi0, c0, budget_s)}
+    O.Oracle.set_threads(1)
+    out["disc_2d_512"]["single_core_mlups"] = rate(m, phi0, c0, budget_s)
+    O.Oracle.set_threads(threads)
+    inst = WL.batch_2d(count=384, seed=1)
+    order = sorted(range(len(inst)), key=lambda i: inst[i].params.nodes)
+    sweep = {}
+    for i in (order[0], order[len(order) // 2], order[-1]):
+        x = inst[i]
+        sweep["%dx%d" % (x.params.nx, x.params.ny)] = rate(x.params, x.phi, x.c, budget_s / 2)
+    out["batch_2d_instance_sweep_mlups"] = sweep
+    out["cores"] = threads
+    return out
 
 
 def run_reference(args):
