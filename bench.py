@@ -525,72 +525,81 @@ def run_ours(args):
     extra = {}
     # FP64 forward on the same GPU, for the FP32/FP64 ratio the metric asks for
     if prec == "fp32" and args.fp64_steps > 0:
-        sim64 = L.Simulation(model, phi0, c0, precision="fp64", stream=stream.cuda_stream, lattice=L.LBPF_D3Q19)
-        sim64.step(2)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        sim64.step(args.fp64_steps)
-        b.record(stream)
-        torch.cuda.synchronize()
-        ms64 = a.elapsed_time(b) / args.fp64_steps
-        sim64.close()
-        extra["fp64_forward"] = {"ms_per_step": ms64, "mlups": N / (ms64 * 1e-3) / 1e6,
-                                 "fp32_speedup": ms64 / ms_per_step,
-                                 "roofline": fp64_roofline(stream, N, ms64, wl.replace("_fp32", "_fp64"))}
+        try:
+            sim64 = L.Simulation(model, phi0, c0, precision="fp64", stream=stream.cuda_stream, lattice=L.LBPF_D3Q19)
+            sim64.step(2)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sim64.step(args.fp64_steps)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms64 = a.elapsed_time(b) / args.fp64_steps
+            sim64.close()
+            extra["fp64_forward"] = {"ms_per_step": ms64, "mlups": N / (ms64 * 1e-3) / 1e6,
+                                     "fp32_speedup": ms64 / ms_per_step,
+                                     "roofline": fp64_roofline(stream, N, ms64, wl.replace("_fp32", "_fp64"))}
+        except Exception as ex:   # reported, never silently dropped
+            extra["fp64_forward"] = {"error": str(ex)}
 
     # the 16-bit deviation-storage variants of the same step, for context
     if prec == "fp32" and args.dev16_steps > 0:
-        dev = {}
-        for p16 in ("fp16dev", "bf16dev"):
-            s16 = L.Simulation(model, phi0, c0, precision=p16, stream=stream.cuda_stream, lattice=L.LBPF_D3Q19,
-                               mass_every=1)
-            s16.step(3)
-            torch.cuda.synchronize()
-            a16, b16 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a16.record(stream)
-            kp, kc, kr = s16.step_timed(args.dev16_steps)
-            b16.record(stream)
-            torch.cuda.synchronize()
-            ms16 = a16.elapsed_time(b16) / args.dev16_steps
-            m0, tgt = s16.solute_mass()
-            s16.close()
-            bp, bc = algorithmic_bytes(q, 4, 2)
-            dev[p16] = {"ms_per_step": ms16, "mlups": N / (ms16 * 1e-3) / 1e6,
-                        "step_frac": (bp + bc) * N / (ms16 * 1e-3) / 1e9 / hbm, "bytes_per_node": bp + bc,
-                        "kernel_ms": {"k_phi_step": kp / args.dev16_steps, "k_c_step": kc / args.dev16_steps},
-                        "mass_drift": (m0 - tgt) / tgt}
-        extra["dev16"] = dev
+        try:
+            dev = {}
+            for p16 in ("fp16dev", "bf16dev"):
+                s16 = L.Simulation(model, phi0, c0, precision=p16, stream=stream.cuda_stream, lattice=L.LBPF_D3Q19,
+                                   mass_every=1)
+                s16.step(3)
+                torch.cuda.synchronize()
+                a16, b16 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a16.record(stream)
+                kp, kc, kr = s16.step_timed(args.dev16_steps)
+                b16.record(stream)
+                torch.cuda.synchronize()
+                ms16 = a16.elapsed_time(b16) / args.dev16_steps
+                m0, tgt = s16.solute_mass()
+                s16.close()
+                bp, bc = algorithmic_bytes(q, 4, 2)
+                dev[p16] = {"ms_per_step": ms16, "mlups": N / (ms16 * 1e-3) / 1e6,
+                            "step_frac": (bp + bc) * N / (ms16 * 1e-3) / 1e9 / hbm, "bytes_per_node": bp + bc,
+                            "kernel_ms": {"k_phi_step": kp / args.dev16_steps, "k_c_step": kc / args.dev16_steps},
+                            "mass_drift": (m0 - tgt) / tgt}
+            extra["dev16"] = dev
+        except Exception as ex:   # reported, never silently dropped
+            extra["dev16"] = {"error": str(ex)}
 
     # the two variants of the composition scheme of Sec. 3 on the same workload:
     # h on D3Q7 (fewer bytes per node) and the alternative equilibrium h^eq,alt
     if prec == "fp32" and args.hvar_steps > 0:
-        import dataclasses
-        hv = {}
-        for name, hl, alt in (("h_d3q7", 1, 0), ("h_eq_alt", 0, 1), ("h_d3q7_eq_alt", 1, 1)):
-            mv = dataclasses.replace(model, h_lattice=hl, h_eq_alt=alt)
-            sv = L.Simulation(mv, phi0, c0, precision="fp32", stream=stream.cuda_stream, lattice=L.LBPF_D3Q19,
-                              mass_every=1)
-            sv.step(3)
-            torch.cuda.synchronize()
-            av, bv = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            av.record(stream)
-            kp, kc, kr = sv.step_timed(args.hvar_steps)
-            bv.record(stream)
-            torch.cuda.synchronize()
-            msv = av.elapsed_time(bv) / args.hvar_steps
-            m0, tgt = sv.solute_mass()
-            sv.close()
-            qh = 7 if hl else 19
-            bp, bc = 2 * q * 4 + 2 * 4, 2 * qh * 4
-            kcm = kc / args.hvar_steps
-            hv[name] = {"h_lattice": "D3Q7" if hl else "D3Q19", "h_eq_alt": alt,
-                        "ms_per_step": msv, "mlups": N / (msv * 1e-3) / 1e6,
-                        "bytes_per_node": bp + bc, "step_frac": (bp + bc) * N / (msv * 1e-3) / 1e9 / hbm,
-                        "k_c_step_frac": bc * N / (kcm * 1e-3) / 1e9 / hbm,
-                        "kernel_ms": {"k_phi_step": kp / args.hvar_steps, "k_c_step": kcm},
-                        "speedup_vs_main": ms_per_step / msv, "mass_drift": (m0 - tgt) / tgt}
-        extra["h_variants"] = hv
+        try:
+            import dataclasses
+            hv = {}
+            for name, hl, alt in (("h_d3q7", 1, 0), ("h_eq_alt", 0, 1), ("h_d3q7_eq_alt", 1, 1)):
+                mv = dataclasses.replace(model, h_lattice=hl, h_eq_alt=alt)
+                sv = L.Simulation(mv, phi0, c0, precision="fp32", stream=stream.cuda_stream, lattice=L.LBPF_D3Q19,
+                                  mass_every=1)
+                sv.step(3)
+                torch.cuda.synchronize()
+                av, bv = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                av.record(stream)
+                kp, kc, kr = sv.step_timed(args.hvar_steps)
+                bv.record(stream)
+                torch.cuda.synchronize()
+                msv = av.elapsed_time(bv) / args.hvar_steps
+                m0, tgt = sv.solute_mass()
+                sv.close()
+                qh = 7 if hl else 19
+                bp, bc = 2 * q * 4 + 2 * 4, 2 * qh * 4
+                kcm = kc / args.hvar_steps
+                hv[name] = {"h_lattice": "D3Q7" if hl else "D3Q19", "h_eq_alt": alt,
+                            "ms_per_step": msv, "mlups": N / (msv * 1e-3) / 1e6,
+                            "bytes_per_node": bp + bc, "step_frac": (bp + bc) * N / (msv * 1e-3) / 1e9 / hbm,
+                            "k_c_step_frac": bc * N / (kcm * 1e-3) / 1e9 / hbm,
+                            "kernel_ms": {"k_phi_step": kp / args.hvar_steps, "k_c_step": kcm},
+                            "speedup_vs_main": ms_per_step / msv, "mass_drift": (m0 - tgt) / tgt}
+            extra["h_variants"] = hv
+        except Exception as ex:   # reported, never silently dropped
+            extra["h_variants"] = {"error": str(ex)}
 
     e4 = None
     if args.e4_steps > 0 and prec == "fp32":
@@ -610,7 +619,7 @@ def run_ours(args):
     if args.adj_steps > 0 and prec == "fp32":
         try:
             adj = adjoint_measurement(args, stream, hbm, b_phi + b_c)
-            if "fp64_forward" in extra:
+            if "ms_per_step" in extra.get("fp64_forward", {}):
                 # per node: the sweep runs on 128^3, the FP64 forward on the main grid
                 adj["adjoint_to_fp64_forward_per_node"] = (adj["adjoint_sweep_ms_per_step"] / adj["nodes"]) / \
                     (extra["fp64_forward"]["ms_per_step"] / N)
