@@ -156,8 +156,11 @@ lbpf_status lbpf_default_params(lbpf_params *p);
 lbpf_status lbpf_create(const lbpf_params *p, const double *phi0, const double *c0,
                         int32_t ptr_is_device, void *cuda_stream, lbpf_ctx **out);
 
-/* Queue nsteps coupled time steps (n -> n + nsteps) on the context's stream.
- * nsteps >= 0.  Errors: EINVAL, ECUDA (launch failure), ESTATE. */
+/* Queue nsteps coupled time steps (n -> n + nsteps) on the context's stream:
+ * each step is the sequence of Sec. 3 listed at the top of this header (the phi
+ * LBE of Sec. 3.2, then the composition LBE of Sec. 3.3 with dphi/dt from this
+ * step's phi), followed by the FP64 mass correction when mass_every divides the
+ * step count.  nsteps >= 0.  Errors: EINVAL, ECUDA (launch failure), ESTATE. */
 lbpf_status lbpf_step(lbpf_ctx *ctx, int64_t nsteps);
 
 /* Total solute sum_x c and phase sum_x phi, accumulated in FP64 on the GPU
