@@ -533,7 +533,9 @@ void or_mu(const or_params *p, const double *phi, const double *c, double *mu)
 /* its adjoint is the chain rule taken back through the operations listed at */
 /* the top of this file, in reverse order.  Parameters differentiated:       */
 /* pb[0] = d/dD_l, pb[1] = d/dtau_g, pb[2] = d/dtau_h, pb[3] = d/dlambda,     */
-/* with W, D_s, the coexistence values and a of j_at held fixed.             */
+/* with W, D_s, the coexistence values, a of j_at and eps_s / eps_l held     */
+/* fixed.  It covers every option of the step (h on D2Q5 / D3Q7, h^eq,alt,  */
+/* unequal curvatures).                                                      */
 /* ======================================================================== */
 #ifndef ORACLE_TANGENT_BUILD
 
@@ -554,11 +556,12 @@ static long downstream_index(const or_params *p, const lattice *L, int j, int x,
 }
 
 /* Adjoint of the pointwise sources at one node.  Given the adjoints Gb[j] of the
- * phi sources G_j, heqb[j] of the equilibria h^eq_j, Hb[j] of the c sources H_j
- * and atb of the anti-trapping magnitude, add the adjoints of phi, mu, n, grad
- * and of the parameters.  (Forward: Sec. 3.2 and Sec. 3.3 formulas above.) */
-static void pointwise_adjoint(const or_params *p, const lattice *L, double phi, double c, double mu,
-                              double dphi, const double grad[3], const double nvec[3],
+ * phi sources G_j (links of L), heqb[j] of the equilibria h^eq_j and Hb[j] of the
+ * flux terms of the h collision (links of LH: H_j = gamma w_j e_j.F, or
+ * A_j = w_j e_j.F / xi_s^2 of h^eq,alt), add the adjoints of phi, mu, n, grad,
+ * dphi and of the parameters.  (Forward: Sec. 2.3, 3.2 and 3.3 formulas above.) */
+static void pointwise_adjoint(const or_params *p, const lattice *L, const lattice *LH, double phi, double c,
+                              double mu, double dphi, const double grad[3], const double nvec[3],
                               const double *Gb, const double *heqb, const double *Hb,
                               double *phib, double *mub, double gradb[3], double nb[3], double *cb,
                               double *dphib, double *pb)
@@ -570,16 +573,27 @@ static void pointwise_adjoint(const or_params *p, const lattice *L, double phi, 
     double gamma = 3.0 / p->tau_h;
     double D = p->D_l * phi + p->D_s * (1.0 - phi);
     double Dprime = p->D_l - p->D_s;
+    /* S = p'(phi) drive(mu), jump(mu) = coefficient of a W dphi n in j_at, and
+     * their mu-derivatives (Eq. SourceTerm_Coexistence / Eq. SourceTerm;
+     * Eq. Anti-trapping_Equilibrium / Eq. Anti-Trapping_Quadratic) */
+    double drive = dc * (mu - p->mu_eq), drive_mu = dc, jump = dc, jump_mu = 0.0;
+    if (p->unequal_eps) {
+        parabolas pq = get_parabolas(p);
+        drive = 0.5 * (pq.e_l - pq.e_s) * mu * mu - (pq.m_l - pq.m_s) * mu - pq.df;
+        drive_mu = (pq.e_l - pq.e_s) * mu - (pq.m_l - pq.m_s);
+        jump = (pq.e_l - pq.e_s) * mu + pq.m_s - pq.m_l;
+        jump_mu = pq.e_l - pq.e_s;
+    }
 
     /* G_j = w_j (Gst + Gcurv_j) */
     double Gstb = 0.0;
     for (int j = 0; j < q; ++j) Gstb += L->w[j] * Gb[j];
-    double S = 6.0 * phi * (1.0 - phi) * dc * (mu - p->mu_eq);
+    double S = 6.0 * phi * (1.0 - phi) * drive;
     double Sb = Gstb * (-p->lambda * M / W2);
     pb[3] += Gstb * (-M * S / W2);
     pb[1] += Gstb * (-p->lambda * S / W2) / 3.0;
-    *phib += Sb * 6.0 * dc * (1.0 - 2.0 * phi) * (mu - p->mu_eq);
-    *mub += Sb * 6.0 * dc * phi * (1.0 - phi);
+    *phib += Sb * 6.0 * (1.0 - 2.0 * phi) * drive;
+    *mub += Sb * 6.0 * phi * (1.0 - phi) * drive_mu;
     if (p->counter_term) {
         double K = (4.0 / p->W) * phi * (1.0 - phi);
         double Kb = 0.0;
@@ -598,25 +612,28 @@ static void pointwise_adjoint(const or_params *p, const lattice *L, double phi, 
         pb[1] += Gcb * (-(8.0 / W2)) * wp / 3.0;
     }
 
-    /* h^eq_0 = c - (1 - w_0) gamma D mu, h^eq_k = w_k gamma D mu */
-    double Qb = -(1.0 - L->w[0]) * heqb[0];
+    /* h^eq_0 = c - (1 - w_0) gamma D mu, h^eq_k = w_k gamma D mu (on LH) */
+    int qh = LH->q;
+    double Qb = -(1.0 - LH->w[0]) * heqb[0];
     *cb += heqb[0];
-    for (int k = 1; k < q; ++k) Qb += L->w[k] * heqb[k];
+    for (int k = 1; k < qh; ++k) Qb += LH->w[k] * heqb[k];
     double gammab = Qb * D * mu;
     double Db = Qb * gamma * mu;
     *mub += Qb * gamma * D;
     *phib += Db * Dprime;
     pb[0] += Db * phi;
 
-    /* H_k = gamma w_k e_k.F, F = mu D' grad + at n, at = s a W dc dphi */
+    /* H_k = gamma w_k e_k.F (or A_k = 3 w_k e_k.F with h^eq,alt),
+     * F = mu D' grad + at n, at = s a W jump(mu) dphi */
     double F[3];
-    double at = p->anti_trapping ? p->a_at * p->W * dc * dphi : 0.0;
+    double at = p->anti_trapping ? p->a_at * p->W * jump * dphi : 0.0;
     for (int a = 0; a < 3; ++a) F[a] = mu * Dprime * grad[a] + at * nvec[a];
     double Fb[3] = {0.0, 0.0, 0.0};
-    for (int k = 0; k < q; ++k) {
-        double eF = L->e[k][0] * F[0] + L->e[k][1] * F[1] + L->e[k][2] * F[2];
-        gammab += L->w[k] * eF * Hb[k];
-        for (int a = 0; a < 3; ++a) Fb[a] += gamma * L->w[k] * L->e[k][a] * Hb[k];
+    double kF = p->h_eq_alt ? 3.0 : gamma;
+    for (int k = 0; k < qh; ++k) {
+        double eF = LH->e[k][0] * F[0] + LH->e[k][1] * F[1] + LH->e[k][2] * F[2];
+        if (!p->h_eq_alt) gammab += LH->w[k] * eF * Hb[k];
+        for (int a = 0; a < 3; ++a) Fb[a] += kF * LH->w[k] * LH->e[k][a] * Hb[k];
     }
     double Fg = Fb[0] * grad[0] + Fb[1] * grad[1] + Fb[2] * grad[2];
     double Fn = Fb[0] * nvec[0] + Fb[1] * nvec[1] + Fb[2] * nvec[2];
@@ -626,13 +643,17 @@ static void pointwise_adjoint(const or_params *p, const lattice *L, double phi, 
         gradb[a] += mu * Dprime * Fb[a];
         nb[a] += at * Fb[a];
     }
-    if (p->anti_trapping) *dphib += p->a_at * p->W * dc * Fn;
+    if (p->anti_trapping) {
+        *dphib += p->a_at * p->W * jump * Fn;
+        *mub += p->a_at * p->W * jump_mu * dphi * Fn;
+    }
     pb[2] += gammab * (-3.0 / (p->tau_h * p->tau_h));
 }
 
 /* Adjoint of the unit normal and of the closure, then the transpose of the
  * gradient stencil: the last three operations of every node, reversed. */
-static void finish_adjoint(const or_params *p, const lattice *L, const double *grad, const double *nvec,
+static void finish_adjoint(const or_params *p, const lattice *L, const double *phi, const double *mu,
+                           const double *grad, const double *nvec,
                            double *gradb, double *nb, double *mub, double *phib, double *cb)
 {
     long N = (long)p->nx * p->ny * p->nz;
@@ -642,8 +663,16 @@ static void finish_adjoint(const or_params *p, const lattice *L, const double *g
         double inv = 1.0 / sqrt(g2 + p->eps_n * p->eps_n);
         double nn = nv[0] * nb[3 * i] + nv[1] * nb[3 * i + 1] + nv[2] * nb[3 * i + 2];
         for (int a = 0; a < 3; ++a) gradb[3 * i + a] += (nb[3 * i + a] - nv[a] * nn) * inv;
-        cb[i] += mub[i];
-        phib[i] += mub[i] * (p->c_s_co - p->c_l_co);
+        if (p->unequal_eps) {
+            /* mu = [c - phi m_l - (1 - phi) m_s] / den, den = e_s phi + e_l (1 - phi) */
+            parabolas pq = get_parabolas(p);
+            double den = pq.e_s * phi[i] + pq.e_l * (1.0 - phi[i]);
+            cb[i] += mub[i] / den;
+            phib[i] += mub[i] * (-(pq.m_l - pq.m_s) - mu[i] * (pq.e_s - pq.e_l)) / den;
+        } else {
+            cb[i] += mub[i];
+            phib[i] += mub[i] * (p->c_s_co - p->c_l_co);
+        }
     }
     for (int z = 0; z < p->nz; ++z)
         for (int y = 0; y < p->ny; ++y)
@@ -665,15 +694,15 @@ static void finish_adjoint(const or_params *p, const lattice *L, const double *g
 int or_step_adjoint(const or_params *p, const double *g, const double *h, const double *phi, const double *c,
                     double *gb, double *hb, double *phib, double *cb, double *pb)
 {
-    if (p->h_lattice || p->h_eq_alt || p->unequal_eps) return -2;   /* the adjoint covers the main scheme only */
     lattice L = get_lattice(p->dim);
+    lattice LH = get_h_lattice(p);
     long N = (long)p->nx * p->ny * p->nz;
-    int q = L.q;
+    int q = L.q, qh = LH.q;
     double omg = 1.0 / (p->tau_g + 0.5), omh = 1.0 / (p->tau_h + 0.5);
     double *mu = malloc(sizeof(double) * N), *grad = malloc(sizeof(double) * 3 * N);
     double *nvec = malloc(sizeof(double) * 3 * N), *gs = malloc(sizeof(double) * q * N);
     double *phinew = malloc(sizeof(double) * N), *Gsum = malloc(sizeof(double) * N);
-    double *gbo = malloc(sizeof(double) * q * N), *hbo = malloc(sizeof(double) * q * N);
+    double *gbo = malloc(sizeof(double) * q * N), *hbo = malloc(sizeof(double) * qh * N);
     double *phibo = calloc(N, sizeof(double)), *cbo = calloc(N, sizeof(double));
     double *mub = calloc(N, sizeof(double)), *gradb = calloc(3 * N, sizeof(double));
     double *nb = calloc(3 * N, sizeof(double)), *dphib = calloc(N, sizeof(double));
@@ -719,20 +748,27 @@ int or_step_adjoint(const or_params *p, const double *g, const double *h, const 
                     double F[3];
                     flux_F(p, mu[i], dphi, grad + 3 * i, nvec + 3 * i, F);
                     double omhb = 0.0;
-                    for (int j = 0; j < q; ++j) {
-                        long y2 = downstream_index(p, &L, j, x, y, z);
-                        hsb[j] = (y2 < 0) ? hb[L.opp[j] * N + i] + cb[i] : hb[j * N + y2] + cb[y2];
-                        double Hj = source_H(p, &L, j, F);
-                        double heq = h_equilibrium(p, &L, j, phi[i], c[i], mu[i]);
+                    for (int j = 0; j < q; ++j) Gb0[j] = 0.0;
+                    for (int j = 0; j < qh; ++j) {
+                        long y2 = downstream_index(p, &LH, j, x, y, z);
+                        hsb[j] = (y2 < 0) ? hb[LH.opp[j] * N + i] + cb[i] : hb[j * N + y2] + cb[y2];
                         hbo[j * N + i] = (1.0 - omh) * hsb[j];
                         heqb[j] = omh * hsb[j];
-                        Hb[j] = (1.0 - 0.5 * omh) * hsb[j];
-                        omhb += hsb[j] * (heq - 0.5 * Hj - h[j * N + i]);
-                        Gb0[j] = 0.0;
+                        if (p->h_eq_alt) {
+                            /* h* = h - omh (h - h^eq,alt): the flux part A_j enters with omh */
+                            double heq = h_equilibrium_alt(p, &LH, j, phi[i], c[i], mu[i], F);
+                            Hb[j] = omh * hsb[j];
+                            omhb += hsb[j] * (heq - h[j * N + i]);
+                        } else {
+                            double Hj = source_H(p, &LH, j, F);
+                            double heq = h_equilibrium(p, &LH, j, phi[i], c[i], mu[i]);
+                            Hb[j] = (1.0 - 0.5 * omh) * hsb[j];
+                            omhb += hsb[j] * (heq - 0.5 * Hj - h[j * N + i]);
+                        }
                     }
                     pb[2] += omhb * (-omh * omh);
-                    pointwise_adjoint(p, &L, phi[i], c[i], mu[i], dphi, grad + 3 * i, nvec + 3 * i, Gb0, heqb, Hb,
-                                      phibo + i, mub + i, gradb + 3 * i, nb + 3 * i, cbo + i, dphib + i, pb);
+                    pointwise_adjoint(p, &L, &LH, phi[i], c[i], mu[i], dphi, grad + 3 * i, nvec + 3 * i, Gb0, heqb,
+                                      Hb, phibo + i, mub + i, gradb + 3 * i, nb + 3 * i, cbo + i, dphib + i, pb);
                 }
         /* phi part, reversed: phi' = sum g' + G/2, stream, collision, sources */
         for (int z = 0; z < p->nz; ++z)
@@ -754,12 +790,13 @@ int or_step_adjoint(const or_params *p, const double *g, const double *h, const 
                     }
                     pb[1] += omgb * (-omg * omg);
                     phibo[i] -= dphib[i];                 /* dphi = phi' - phi */
-                    pointwise_adjoint(p, &L, phi[i], c[i], mu[i], 0.0, grad + 3 * i, nvec + 3 * i, Gb, zero, zero,
-                                      phibo + i, mub + i, gradb + 3 * i, nb + 3 * i, cbo + i, &dummy, pb);
+                    for (int j = q; j < 19; ++j) zero[j] = 0.0;
+                    pointwise_adjoint(p, &L, &LH, phi[i], c[i], mu[i], 0.0, grad + 3 * i, nvec + 3 * i, Gb, zero,
+                                      zero, phibo + i, mub + i, gradb + 3 * i, nb + 3 * i, cbo + i, &dummy, pb);
                 }
-        finish_adjoint(p, &L, grad, nvec, gradb, nb, mub, phibo, cbo);
+        finish_adjoint(p, &L, phi, mu, grad, nvec, gradb, nb, mub, phibo, cbo);
         memcpy(gb, gbo, sizeof(double) * q * N);
-        memcpy(hb, hbo, sizeof(double) * q * N);
+        memcpy(hb, hbo, sizeof(double) * qh * N);
         memcpy(phib, phibo, sizeof(double) * N);
         memcpy(cb, cbo, sizeof(double) * N);
     }
@@ -774,10 +811,10 @@ int or_step_adjoint(const or_params *p, const double *g, const double *h, const 
 int or_init_adjoint(const or_params *p, const double *phi0, const double *c0, const double *gb, const double *hb,
                     double *phib, double *cb, double *pb)
 {
-    if (p->h_lattice || p->h_eq_alt || p->unequal_eps) return -2;
     lattice L = get_lattice(p->dim);
+    lattice LH = get_h_lattice(p);
     long N = (long)p->nx * p->ny * p->nz;
-    int q = L.q;
+    int q = L.q, qh = LH.q;
     double *mu = malloc(sizeof(double) * N), *grad = malloc(sizeof(double) * 3 * N);
     double *nvec = malloc(sizeof(double) * 3 * N), *mub = calloc(N, sizeof(double));
     double *gradb = calloc(3 * N, sizeof(double)), *nb = calloc(3 * N, sizeof(double));
@@ -792,18 +829,21 @@ int or_init_adjoint(const or_params *p, const double *phi0, const double *c0, co
                     normal_from(p, grad + 3 * i, nvec + 3 * i);
                 }
         for (long i = 0; i < N; ++i) {
-            /* g_k = w_k phi0 - G_k/2,  h_k = h^eq_k - H_k/2 with dphi/dt = 0 */
+            /* g_k = w_k phi0 - G_k/2;  h_k = h^eq_k - H_k/2 with dphi/dt = 0, or
+             * h_k = h^eq_k + A_k (h^eq,alt) */
             double Gb[19], heqb[19], Hb[19], dummy = 0.0;
             for (int j = 0; j < q; ++j) {
                 phib[i] += L.w[j] * gb[j * N + i];
                 Gb[j] = -0.5 * gb[j * N + i];
-                heqb[j] = hb[j * N + i];
-                Hb[j] = -0.5 * hb[j * N + i];
             }
-            pointwise_adjoint(p, &L, phi0[i], c0[i], mu[i], 0.0, grad + 3 * i, nvec + 3 * i, Gb, heqb, Hb,
+            for (int j = 0; j < qh; ++j) {
+                heqb[j] = hb[j * N + i];
+                Hb[j] = (p->h_eq_alt ? 1.0 : -0.5) * hb[j * N + i];
+            }
+            pointwise_adjoint(p, &L, &LH, phi0[i], c0[i], mu[i], 0.0, grad + 3 * i, nvec + 3 * i, Gb, heqb, Hb,
                               phib + i, mub + i, gradb + 3 * i, nb + 3 * i, cb + i, &dummy, pb);
         }
-        finish_adjoint(p, &L, grad, nvec, gradb, nb, mub, phib, cb);
+        finish_adjoint(p, &L, phi0, mu, grad, nvec, gradb, nb, mub, phib, cb);
     }
     free(mu); free(grad); free(nvec); free(mub); free(gradb); free(nb);
     return rc;

@@ -309,8 +309,6 @@ def step_adjoint(p: OracleParams, g, h, phi, c, gb, hb, phib, cb):
     st = [np.ascontiguousarray(a, dtype=np.float64) for a in (g, h, phi, c)]
     pb = np.zeros(4)
     rc = _load().or_step_adjoint(ctypes.byref(cp), *[_dp(a) for a in st], *[_dp(a) for a in arrs], _dp(pb))
-    if rc == -2:
-        raise NotImplementedError("the oracle adjoint covers h on the g lattice with H_k only")
     if rc != 0:
         raise MemoryError("oracle adjoint failed")
     return (*arrs, pb)
@@ -328,8 +326,6 @@ def init_adjoint(p: OracleParams, phi0, c0, gb, hb, phib, cb):
     pb = np.zeros(4)
     rc = _load().or_init_adjoint(ctypes.byref(cp), _dp(phi0), _dp(c0), _dp(gb), _dp(hb), _dp(phib), _dp(cb),
                                  _dp(pb))
-    if rc == -2:
-        raise NotImplementedError("the oracle adjoint covers h on the g lattice with H_k only")
     if rc != 0:
         raise MemoryError("oracle adjoint failed")
     return phib, cb, pb
