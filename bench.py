@@ -79,6 +79,16 @@ def whole_job_mlups(nodes_per_rank: int, steps: int, world: int, job_ms: float) 
     return world * nodes_per_rank * steps / (job_ms * 1e-3) / 1e6
 
 
+def dram_throughput(traffic_bytes, kernel_ms, peak_gbs):
+    """Actual DRAM throughput of a kernel: its ncu bytes per launch over its mean
+    event-timed duration, in GB/s and as a fraction of the peak (None when the
+    committed capture does not match the current kernel sources)."""
+    if not traffic_bytes or not kernel_ms or kernel_ms <= 0:
+        return None
+    gbs = traffic_bytes / (kernel_ms * 1e-3) / 1e9
+    return {"gbs": gbs, "frac": gbs / peak_gbs}
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -516,6 +526,7 @@ def run_ours(args):
     roof = {"bound": "hbm", "kernel": dom[0], "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "peak_source": hbm_src + " (MEASURED_PEAKS.json hbm_gbs)" if hbm_src == "measured" else "fallback",
             "traffic": ncu_traffic(dom[0], wl),
+            "traffic_throughput": dram_throughput(ncu_traffic(dom[0], wl), dom[1], hbm),
             "bytes_per_node": dom[2],
             "step": {"achieved": step_bytes / (ms_per_step * 1e-3) / 1e9,
                      "frac": step_bytes / (ms_per_step * 1e-3) / 1e9 / hbm, "bytes_per_node": b_phi + b_c},

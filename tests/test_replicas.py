@@ -53,3 +53,4 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
     class A:
         n, steps, warmup = 256, 1, 0
     assert bench.run_reference(A()) is None
+
