@@ -99,6 +99,23 @@ def test_gradient_mirror_ghost_at_wall():
     assert np.allclose(g[1:-1], 0.5 * ((x[2:]) ** 2 - (x[:-2]) ** 2), atol=1e-13)
 
 
+def test_gradient_mirror_ghost_at_a_z_wall_3d():
+    """The same on D3Q19 across a wall in z (the axis the GPU kernels march
+    along), with phi = z^2 on a walled z axis: grad_z is one-sided at both walls
+    and central inside (the edge links contribute the same differences), and the
+    in-plane components vanish."""
+    n = 8
+    p = O.OracleParams(nx=4, ny=6, nz=n, bc=(0, 0, 1))
+    z = np.arange(n, dtype=float)
+    phi = np.broadcast_to((z * z)[:, None, None], (n, 6, 4)).copy()
+    g = O.gradient(p, phi)
+    gz = g[:, 2, 1, 2]
+    assert gz[0] == pytest.approx(0.5, abs=1e-14)
+    assert gz[-1] == pytest.approx(0.5 * ((n - 1) ** 2 - (n - 2) ** 2), abs=1e-13)
+    assert np.allclose(gz[1:-1], 0.5 * (z[2:] ** 2 - z[:-2] ** 2), atol=1e-13)
+    assert np.abs(g[..., 0]).max() < 1e-14 and np.abs(g[..., 1]).max() < 1e-14
+
+
 # ---- closed forms --------------------------------------------------------------
 
 def test_printed_roots_and_lambda_star():
