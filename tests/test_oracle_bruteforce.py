@@ -1,8 +1,10 @@
 """Brute-force pin of the oracle: one step of Sec. 3 written again, independently,
-as whole-array NumPy (periodic shifts with np.roll instead of the oracle's
-per-node C loops and index maps), on tiny periodic grids (4 x 4, 5 x 3,
-3 x 3 x 3, 4 x 3 x 5), for the main scheme and every option: both phi
-equations, anti-trapping, h on D2Q5 / D3Q7, h^eq,alt and unequal curvatures.
+as whole-array NumPy (shifts with np.roll, mirror ghosts with np.pad, bounce-back
+as a mask, instead of the oracle's per-node C loops and index maps), on tiny
+grids (4 x 4, 5 x 3, 3 x 3 x 3, 4 x 3 x 5 periodic; 6 x 5, 7 x 4, 5 x 3 x 4 and
+3 x 4 x 5 with bounce-back walls on one or two axes), for the main scheme and
+every option: both phi equations, anti-trapping, h on D2Q5 / D3Q7, h^eq,alt and
+unequal curvatures.
 
 The initial populations and one step must agree with the oracle to rounding
 (1e-13 relative; the two sum in different orders).  Catches an index, offset
@@ -20,9 +22,42 @@ from paper_2111_05960_gb300 import workloads as WL
 TOL = 1e-13
 
 
+BC = (0, 0, 0)   # set per test: 0 periodic, 1 half-way bounce-back, per axis (x, y, z)
+
+
 def _shift(a, e):
-    """a(x + e) for every x (periodic); a has the grid as its last three axes (z, y, x)."""
-    return np.roll(a, shift=(-e[2], -e[1], -e[0]), axis=(-3, -2, -1))
+    """a(x + e) for every x on the phi stencil: periodic, or across a wall the mirror
+    ghost a(-1) = a(0), a(-2) = a(1) (np.pad 'symmetric'); a has the grid as its
+    last three axes (z, y, x)."""
+    out = a
+    for ax, (d, bc) in enumerate(zip((e[2], e[1], e[0]), (BC[2], BC[1], BC[0]))):
+        axis = ax - 3
+        if d == 0:
+            continue
+        if bc == 0:
+            out = np.roll(out, -d, axis=axis)
+        else:
+            n = out.shape[axis]
+            pad = [(0, 0)] * out.ndim
+            pad[axis] = (2, 2)
+            padded = np.pad(out, pad, mode="symmetric")
+            out = np.take(padded, np.arange(n) + 2 + d, axis=axis)
+    return out
+
+
+def _stream(fs, e, opp):
+    """f_k(x) = f*_k(x - e_k), or f*_{opp k}(x) when x - e_k lies beyond a wall."""
+    out = np.empty_like(fs)
+    for k in range(fs.shape[0]):
+        src = np.roll(fs[k], shift=(e[k][2], e[k][1], e[k][0]), axis=(-3, -2, -1))
+        nz, ny, nx = fs.shape[1:]
+        z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+        outside = np.zeros((nz, ny, nx), dtype=bool)
+        for c, n, d, bc in ((x, nx, e[k][0], BC[0]), (y, ny, e[k][1], BC[1]), (z, nz, e[k][2], BC[2])):
+            if bc:
+                outside |= (c - d < 0) | (c - d >= n)
+        out[k] = np.where(outside, fs[opp[k]], src)
+    return out
 
 
 def _parabolas(p):
@@ -49,6 +84,10 @@ def _tables(p):
     else:
         eh, wh = e, w
     return e, w, eh, wh
+
+
+def _opposite(e):
+    return np.array([next(j for j in range(len(e)) if np.all(e[j] == -e[k])) for k in range(len(e))])
 
 
 def _sources(p, e, w, eh, wh, phi, c, dphi):
@@ -113,12 +152,12 @@ def np_step(p, g, h, phi, c):
     omg, omh = 1 / (p.tau_g + 0.5), 1 / (p.tau_h + 0.5)
     G, _, _, _ = _sources(p, e, w, eh, wh, phi, c, 0.0 * phi)
     gs = g - omg * (g - (w[:, None, None, None] * phi - 0.5 * G)) + G
-    g1 = np.stack([_shift(gs[k], -e[k]) for k in range(len(w))])     # g_k(x) = g*_k(x - e_k)
+    g1 = _stream(gs, e, _opposite(e))
     phi1 = g1.sum(0) + 0.5 * G.sum(0)
     _, heq, eF, gamma = _sources(p, e, w, eh, wh, phi, c, phi1 - phi)
     target, H = _h_target(p, wh, heq, eF, gamma)
     hs = h - omh * (h - target) + H
-    h1 = np.stack([_shift(hs[k], -eh[k]) for k in range(len(wh))])
+    h1 = _stream(hs, eh, _opposite(eh))
     return g1, h1, phi1, h1.sum(0)
 
 
@@ -133,14 +172,18 @@ OPTIONS = [
 ]
 
 
-@pytest.mark.parametrize("shape", [(1, 4, 4), (1, 3, 5), (3, 3, 3), (5, 3, 4)])
+@pytest.mark.parametrize("shape,bc", [((1, 4, 4), (0, 0, 0)), ((1, 3, 5), (0, 0, 0)), ((3, 3, 3), (0, 0, 0)),
+                                      ((5, 3, 4), (0, 0, 0)), ((1, 5, 6), (1, 1, 0)), ((1, 4, 7), (1, 0, 0)),
+                                      ((4, 3, 5), (1, 0, 1)), ((5, 4, 3), (0, 1, 1))])
 @pytest.mark.parametrize("opts", OPTIONS)
-def test_one_step_matches_independent_numpy(shape, opts):
+def test_one_step_matches_independent_numpy(shape, bc, opts):
+    global BC
+    BC = bc
     nz, ny, nx = shape
     base = dict(tau_g=0.7, tau_h=0.9, W=3.0, lam=4.0, D_l=0.15, D_s=0.03, counter_term=1,
                 anti_trapping=1, a_at=0.2, eps_n=1e-3)
     base.update(opts)
-    p = O.OracleParams(nx=nx, ny=ny, nz=nz, **base)
+    p = O.OracleParams(nx=nx, ny=ny, nz=nz, bc=bc, **base)
     phi0, c0 = WL.random_fields(shape, seed=nx + 7 * ny + 31 * nz, smooth=False)
     o = O.Oracle(p, phi0, c0)
     g0, h0 = np_init(p, phi0, c0)
