@@ -209,6 +209,15 @@ def make_workload(n):
     return WL.porous_3d(n=n)
 
 
+def workload_config(model):
+    """The workload both arms run, by what it is (the same dict for the GPU arm
+    and the oracle arm; the arithmetic type is the line's dtype)."""
+    return {"workload": "porous_3d_%d_d3q19" % model.nx, "nodes": model.nodes, "lattice": "D3Q19",
+            "porosity": 0.35, "W": model.W, "D_l": model.D_l, "D_s": model.D_s,
+            "counter_term": model.counter_term, "anti_trapping": model.anti_trapping,
+            "boundaries": "periodic", "inputs": "seeded Gaussian-random-field medium (PCG64 seed 0)"}
+
+
 def algorithmic_bytes(q: int, real: int, store: int):
     """Bytes per node of each kernel: populations read once and written once, phi^n
     read and phi^{n+1} written by the phi kernel (mu is recomputed from c and phi)."""
@@ -435,6 +444,9 @@ def oracle_other_configs(budget_s=1.5):
 
 
 def run_reference(args):
+    """The FP64 CPU oracle, as it stands, on the same workload and the full grid,
+    on the host cores: W untimed warm-up steps, then K timed steps; value and
+    ms_per_step are those of the timed steps on the whole grid."""
     rank, world, local = dist_env()
     if rank != 0:
         return
@@ -442,26 +454,57 @@ def run_reference(args):
     import oracle as O
     O.build()
     names = O.OracleParams.__dataclass_fields__
-    nz = 16
     p = O.OracleParams(**{k: getattr(model, k) for k in names})
-    p.nz = nz
-    o = O.Oracle(p, np.ascontiguousarray(phi0[:nz]), np.ascontiguousarray(c0[:nz]))
-    o.step(max(args.warmup, 1) if args.warmup > 0 else 0)
+    o = O.Oracle(p, phi0, c0)
+    if args.warmup > 0:
+        o.step(args.warmup)
     t = time.perf_counter()
     o.step(args.steps)
     el = time.perf_counter() - t
-    nodes = p.nx * p.ny * nz
+    nodes = model.nodes
     mlups = nodes * args.steps / el / 1e6
+    cores = O.Oracle.threads()
     out = {"impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": world,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps * (args.n / nz),
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic",
-           "config": {"workload": "porous_3d_256_d3q19", "sample": "%dx%dx%d z-slab" % (p.nx, p.ny, nz),
-                      "parallelism": "host threads"},
-           "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": O.Oracle.threads(), "kind": "oracle",
-                            "sample": "%dx%dx%d z-slab of the 256^3 medium, %d FP64 steps" % (p.nx, p.ny, nz, args.steps)},
+           "data": "synthetic", "config": workload_config(model), "parallelism": "%d host threads (OpenMP)" % cores,
+           "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                            "sample": "the whole %dx%dx%d grid, %d FP64 steps after %d warm-up steps, %.1f s"
+                                      % (p.nx, p.ny, p.nz, args.steps, args.warmup, el),
+                            "cpu_model": cpu_model()},
            "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
+
+
+def compact_legs(out):
+    """The headline numbers of each optional leg, rounded, in one small dict."""
+    def g(d, *path):
+        for k in path:
+            if not isinstance(d, dict) or k not in d:
+                return None
+            d = d[k]
+        return round(d, 4) if isinstance(d, float) else d
+    r = out.get("roofline") or {}
+    legs = {"step_glups": g(out, "value") and round(out["value"] / 1e3, 3),
+            "k_c_step_frac": g(r, "frac") if r.get("kernel") == "k_c_step" else None,
+            "kernel_ms": {k: round(v, 4) for k, v in (r.get("kernel_ms") or {}).items()},
+            "step_frac": g(r, "step", "frac"),
+            "fp64_glups": g(out, "fp64_forward", "mlups") and round(out["fp64_forward"]["mlups"] / 1e3, 3),
+            "fp32_over_fp64": g(out, "fp64_forward", "fp32_speedup"),
+            "fp64_alu_frac": g(out, "fp64_forward", "roofline", "frac"),
+            "batch_2d_glups": g(out, "batch_2d", "mlups") and round(out["batch_2d"]["mlups"] / 1e3, 3),
+            "batch_2d_frac": g(out, "batch_2d", "frac"),
+            "adjoint_to_forward": g(out, "adjoint", "adjoint_to_forward"),
+            "adjoint_reverse_frac": g(out, "adjoint", "reverse_frac"),
+            "e2e_glups": g(out, "e2e", "value") and round(out["e2e"]["value"] / 1e3, 3),
+            "paper_e4_fp32_seconds": g(out, "paper_e4", "fp32_counter_term", "seconds")}
+    for p16 in ("fp16dev", "bf16dev"):
+        legs[p16 + "_glups"] = g(out, "dev16", p16, "mlups") and round(out["dev16"][p16]["mlups"] / 1e3, 3)
+        legs[p16 + "_step_frac"] = g(out, "dev16", p16, "step_frac")
+    for hv in ("h_d3q7", "h_eq_alt"):
+        legs[hv + "_glups"] = g(out, "h_variants", hv, "mlups") and round(out["h_variants"][hv]["mlups"] / 1e3, 3)
+    legs["h_d3q7_k_c_step_frac"] = g(out, "h_variants", "h_d3q7", "k_c_step_frac")
+    return legs
 
 
 def run_ours(args):
@@ -503,12 +546,19 @@ def run_ours(args):
     time.sleep(0.3)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     m_before, m_target = sim.solute_mass()
+    barrier()
+    # the timed region: the product call, lbpf_step (K steps queued on the
+    # library's stream, replayed from the captured two-step graph), bracketed by
+    # two events on that stream
     ev0.record(stream)
-    k_phi_ms, k_c_ms, k_corr_ms = sim.step_timed(args.steps)
+    sim.step(args.steps)
     ev1.record(stream)
     barrier()
     clk = clocks.stop()
     ms = max_over_ranks(ev0.elapsed_time(ev1), world)
+    # the per-kernel split of the same steps (events around every launch,
+    # lbpf_step_timed), taken right after the timed region for the roofline
+    k_phi_ms, k_c_ms, k_corr_ms = sim.step_timed(args.steps)
     m_c, m_phi = sim.mass()
     m_after, _ = sim.solute_mass()
     sim.close()
@@ -531,7 +581,9 @@ def run_ours(args):
             "step": {"achieved": step_bytes / (ms_per_step * 1e-3) / 1e9,
                      "frac": step_bytes / (ms_per_step * 1e-3) / 1e9 / hbm, "bytes_per_node": b_phi + b_c},
             "kernel_ms": {"k_phi_step": avg_phi, "k_c_step": avg_c,
-                          "mass_correction": k_corr_ms / args.steps}}
+                          "mass_correction": k_corr_ms / args.steps},
+            "kernel_timing": "CUDA events around each launch on the library's stream (lbpf_step_timed), "
+                             "%d steps right after the timed region" % args.steps}
 
     extra = {}
     # FP64 forward on the same GPU, for the FP32/FP64 ratio the metric asks for
@@ -677,11 +729,10 @@ def run_ours(args):
                "dtype": {"fp32": "f32", "fp64": "f64", "fp16dev": "f32 (f16 deviation storage)",
                          "bf16dev": "f32 (bf16 deviation storage)"}[prec],
                "data": "synthetic",
-               "config": {"workload": wl, "nodes": N, "lattice": "D3Q19", "porosity": 0.35, "W": model.W,
-                          "D_l": 0.1, "D_s": 0.0, "counter_term": 1, "anti_trapping": 1,
-                          "parallelism": "replicas" if world > 1 else "single GPU",
-                          "l2": "state %.1f GB per buffer set, larger than L2 (no flush needed)"
-                                % (N * (2 * q * store + 2 * real) / 1e9)},
+               "config": workload_config(model),
+               "parallelism": "replicas" if world > 1 else "single GPU",
+               "l2": "state %.1f GB per buffer set, larger than L2 (no flush needed)"
+                     % (N * (2 * q * store + 2 * real) / 1e9),
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "batch_2d": batch, "adjoint": adj, "paper_e4": e4,
                "gpu_launches": (4 if mass_every else 2) * args.steps, "clocks": clk,
                "mass": {"solute_before": m_before, "solute_after": m_after,
@@ -689,6 +740,9 @@ def run_ours(args):
                         "correction": "FP64, every step" if mass_every else "off",
                         "sum_c_field": m_c, "sum_phi": m_phi}}
         out.update(extra)
+        # compact figures of every leg, last on the line so that a reader that
+        # keeps only the end of the output still has them
+        out["legs"] = compact_legs(out)
         print(json.dumps(out))
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -41,8 +41,8 @@
  *     graph (when every step has the same kernels: mass_every <= 1); the first
  *     call that captures must not itself run inside another capture.
  *   - One context must not be used by two threads at once.
- *   - After LBPF_EUNSTABLE or LBPF_ETIMEOUT the context is poisoned: every later
- *     call except lbpf_last_error and lbpf_destroy returns LBPF_ESTATE.
+ *   - After LBPF_EUNSTABLE the context is poisoned: every later call except
+ *     lbpf_last_error, lbpf_get_step and lbpf_destroy returns LBPF_ESTATE.
  */
 #ifndef LBPF_H
 #define LBPF_H
@@ -59,7 +59,8 @@ typedef enum {
     LBPF_ENOMEM = 2,      /* device allocation failed; nothing leaked */
     LBPF_ECUDA = 3,       /* a CUDA call failed; message in lbpf_last_error */
     LBPF_EUNSTABLE = 4,   /* non-finite field or phi far outside [0, 1] */
-    LBPF_ETIMEOUT = 5,    /* a bounded device wait ran out */
+                          /* 5 is unused: no kernel of this library waits on
+                             another block, stream or device, so no call times out */
     LBPF_ESTATE = 6,      /* context poisoned by an earlier error */
     LBPF_EUNSUPPORTED = 7 /* option combination not built */
 } lbpf_status;
@@ -276,9 +277,9 @@ lbpf_status lbpf_batch_solute_mass(lbpf_ctx *ctx, double *masses);
 /* The sums of lbpf_mass (sum c, sum phi, count of bad nodes) over caller-owned
  * device arrays, without allocating anything.  The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc, such as code
- * running inside a host callback or a CUDA-graph node where allocation is not
- * allowed, a monitor that must never block on the allocator, or an embedding
- * runtime that owns all device memory.
+ * running inside a host callback where allocation is not allowed, a monitor that
+ * must never block on the allocator, or an embedding runtime that owns all
+ * device memory.
  *   c, phi      device arrays of n elements, FP64 (precision = LBPF_FP64) or FP32
  *               (precision = LBPF_FP32), e.g. fields from lbpf_get_fields.
  *   out_device  device array of 3 doubles: sum c, sum phi, and the number of
@@ -286,9 +287,11 @@ lbpf_status lbpf_batch_solute_mass(lbpf_ctx *ctx, double *masses);
  *   cuda_stream the stream the two kernels are queued on (NULL = default);
  *               the call returns without synchronising.
  * Scratch: a file-scope device array of 4096 x 3 doubles (96 KiB), present on
- * every GPU that loads the library until the process exits.  The first call on
- * a device looks up that array's device address (cudaGetSymbolAddress) and
- * caches it, so make the first call on each device before any stream capture.
+ * every GPU that loads the library until the process exits.  The first call in
+ * each CUDA context (a device's primary context, a new one after
+ * cudaDeviceReset, or a context the caller made current) looks up that array's
+ * device address there (cudaGetSymbolAddress) and caches it under the
+ * context's id, so make that first call before any stream capture.
  * Every call shares the array and leaves its partial sums in it; nothing in it
  * needs clearing, because each call overwrites the slots it reads.  Calls whose
  * kernels overlap on the GPU (other streams, other threads) race on the array

@@ -40,6 +40,7 @@ class LbpfTrajectory(torch.autograd.Function):
         L.lbpf_get_fields(sim.ctx, phi, c, None, 1)
         fctx.sim = sim
         fctx.theta_dtype = theta.dtype
+        fctx.theta_device = theta.device
         return phi, c
 
     @staticmethod
@@ -53,7 +54,8 @@ class LbpfTrajectory(torch.autograd.Function):
         pv = L.lbpf_adjoint_step(sim.ctx, gphi, gc, dphi0, dc0, 1)
         sim.close()
         fctx.sim = None
-        dtheta = torch.tensor(np.asarray(pv[:4]), dtype=fctx.theta_dtype)
+        # the gradient lives where theta does (the autograd engine checks it)
+        dtheta = torch.tensor(np.asarray(pv[:4]), dtype=fctx.theta_dtype, device=fctx.theta_device)
         return dphi0, dc0, dtheta, None, None, None, None, None
 
 

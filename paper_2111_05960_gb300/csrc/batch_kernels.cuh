@@ -66,18 +66,20 @@ k_batch_step(const BatchInst* __restrict__ inst, const int* __restrict__ tile_in
         const bool walls = I.walls != 0;
         __syncthreads();
         const typename SP::real* pn1 = phi_np1 ? phi_np1 + fo : nullptr;
+        const int z1 = min(z0 + ROWS, sK.P.nz);
+        MassAcc<typename SP::real> macc{0, 0};
         if (walls)
-            march<D2Q9R, SP, 1, ROWS, IS_PHI, true, BX, int, D2Q9R, false>(sK, fin + po, fout + po, phi_n + fo, pn1, c_n + fo,
-                                                        moment_out + fo, nullptr, x0, 0, z0, 0);
+            march<D2Q9R, SP, 1, IS_PHI, true, BX, int, D2Q9R, false>(sK, fin + po, fout + po, phi_n + fo, pn1, c_n + fo,
+                                                                     moment_out + fo, macc, x0, 0, z0, z1);
         else
-            march<D2Q9R, SP, 1, ROWS, IS_PHI, false, BX, int, D2Q9R, false>(sK, fin + po, fout + po, phi_n + fo, pn1, c_n + fo,
-                                                         moment_out + fo, nullptr, x0, 0, z0, 0);
+            march<D2Q9R, SP, 1, IS_PHI, false, BX, int, D2Q9R, false>(sK, fin + po, fout + po, phi_n + fo, pn1,
+                                                                      c_n + fo, moment_out + fo, macc, x0, 0, z0, z1);
     }
 }
 
 template <class SP, int BX, int ROWS>
 constexpr size_t batch_smem(bool is_phi) {
-    return march_smem<D2Q9R, SP, 1, ROWS, BX>(is_phi);
+    return march_smem<D2Q9R, SP, 1, BX>(is_phi);
 }
 
 }  // namespace lbpf

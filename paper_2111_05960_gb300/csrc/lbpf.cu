@@ -160,14 +160,16 @@ struct Impl {
     using TC = TileCfgC<L, sizeof(R) == 8, HS>;
     static constexpr int BX = T::BX, BY = T::BY, ZCH = T::ZCH, MINB = T::MINB;
     static constexpr int BYC = TC::BY, ZCHC = TC::ZCH, MINBC = TC::MINB;
-    static constexpr size_t smem_phi = march_smem<ML, SP, BY, ZCH, BX>(true);
-    static constexpr size_t smem_c = march_smem<ML, SP, BYC, ZCHC, BX>(false);
+    static constexpr size_t smem_phi = march_smem<ML, SP, BY, BX>(true);
+    static constexpr size_t smem_c = march_smem<ML, SP, BYC, BX>(false);
     template <bool W>
-    static constexpr auto kphi() { return k_phi_step<ML, SP, BY, ZCH, MINB, W, BX>; }
+    static constexpr auto kphi() { return k_phi_step<ML, SP, BY, MINB, W, BX>; }
     template <bool W>
-    static constexpr auto kc() { return k_c_step<ML, SP, BYC, ZCHC, MINBC, W, BX, MLH>; }
+    static constexpr auto kc() { return k_c_step<ML, SP, BYC, MINBC, W, BX, MLH>; }
 
     static lbpf_status prepare(lbpf_ctx* ctx) {
+        ctx->zch_phi = ZCH;
+        ctx->zch_c = ZCHC;
         LBPF_CUDA(ctx, cudaFuncSetAttribute(kphi<true>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_phi));
         LBPF_CUDA(ctx, cudaFuncSetAttribute(kc<true>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
         LBPF_CUDA(ctx, cudaFuncSetAttribute(kphi<false>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_phi));
@@ -181,24 +183,24 @@ struct Impl {
     // grid over the marching view (kpm: 2-D domains as [ny][1][nx])
     static dim3 grid(const lbpf_ctx* ctx) {
         const StepParams& P = ctx->kpm.P;
-        return dim3((P.nx + BX - 1) / BX, (P.ny + BY - 1) / BY, (P.nz + ZCH - 1) / ZCH);
+        return dim3((P.nx + BX - 1) / BX, (P.ny + BY - 1) / BY, (P.nz + ctx->zch_phi - 1) / ctx->zch_phi);
     }
     static dim3 grid_c(const lbpf_ctx* ctx) {
         const StepParams& P = ctx->kpm.P;
-        return dim3((P.nx + BX - 1) / BX, (P.ny + BYC - 1) / BYC, (P.nz + ZCHC - 1) / ZCHC);
+        return dim3((P.nx + BX - 1) / BX, (P.ny + BYC - 1) / BYC, (P.nz + ctx->zch_c - 1) / ctx->zch_c);
     }
     static void launch_phi_p(lbpf_ctx* ctx, const void* g, void* g_out, const void* phi, const void* c,
                              void* phi_out) {
         auto kern = walls(ctx) ? kphi<true>() : kphi<false>();
         kern<<<grid(ctx), dim3(BX, BY), smem_phi, ctx->stream>>>(ctx->kpm, (const S*)g, (S*)g_out, (const R*)phi,
-                                                                   (const R*)c, (R*)phi_out);
+                                                                   (const R*)c, (R*)phi_out, ctx->zch_phi);
     }
     static void launch_c_p(lbpf_ctx* ctx, const void* h, void* h_out, const void* phi, const void* phi_out,
                            const void* c, void* c_out, double* mass_partials) {
         auto kern = walls(ctx) ? kc<true>() : kc<false>();
         kern<<<grid_c(ctx), dim3(BX, BYC), smem_c, ctx->stream>>>(ctx->kpm, (const S*)h, (S*)h_out, (const R*)phi,
                                                                  (const R*)phi_out, (const R*)c, (R*)c_out,
-                                                                 mass_partials);
+                                                                 mass_partials, ctx->zch_c);
     }
     static void launch_phi(lbpf_ctx* ctx, int cur) {
         const int nxt = cur ^ 1;
@@ -426,7 +428,7 @@ lbpf_status run_steps(lbpf_ctx* ctx, int64_t nsteps) {
         return check_launch(ctx, "step kernels");
     }
     const bool graphable = ctx->stream != nullptr && !ctx->graph_failed &&
-                           (ctx->p.mass_every <= 1 || ctx->is_batch) && nsteps >= 4;
+                           (ctx->p.mass_every <= 1 || ctx->is_batch) && nsteps >= 3;
     if (!graphable) {
         for (int64_t s = 0; s < nsteps; ++s) launch_one_step(ctx);
         return check_launch(ctx, "step kernels");

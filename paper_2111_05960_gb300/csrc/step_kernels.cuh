@@ -695,10 +695,10 @@ __device__ __forceinline__ void block_mass_out(const MassAcc<R>& m, double* __re
     }
 }
 
-// One z-marching pass of either kernel.  The composition kernel also sums the
-// exact mass of the populations it writes into mass_partials (one FP64 value
-// per block) when that pointer is not null.
-template <class L, class SP, int BY, int ZCH, bool IS_PHI, bool WALLS, int BX = 32, typename I = long long,
+// One z-marching pass of either kernel over the planes z0 <= z < z1 of the tile
+// at (x0, y0).  The composition kernel also adds the exact mass of the
+// populations it writes to macc.
+template <class L, class SP, int BY, bool IS_PHI, bool WALLS, int BX = 32, typename I = long long,
           class LH = L, bool U = true>
 __device__ __forceinline__ void march(const KParams& K, const typename SP::store_t* __restrict__ fin,
                                       typename SP::store_t* __restrict__ fout,
@@ -706,8 +706,7 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
                                       const typename SP::real* __restrict__ phi_np1,
                                       const typename SP::real* __restrict__ c_n,
                                       typename SP::real* __restrict__ moment_out,
-                                      double* __restrict__ mass_partials, int x0, int y0, int z0,
-                                      long long mass_slot) {
+                                      MassAcc<typename SP::real>& macc, int x0, int y0, int z0, int z1) {
     using R = typename SP::real;
     using G = Geo<L, BY, BX>;
     const StepParams& P = K.P;
@@ -728,7 +727,6 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
     static_assert(IS_PHI ? std::is_same<L, LH>::value : L::FLAT_Y == LH::FLAT_Y, "h lattice");
     using LP = LH;
     PullState<LP, SP, IS_PHI, WALLS, I> st;
-    MassAcc<R> macc{R(0), R(0)};
 
     // the ring inputs of plane zg go to stage buffer zg & 1
     HaloOffsets<G> halo;
@@ -753,9 +751,9 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
     // z-march.  While plane z is pulled, the phi plane z+3 and the ring of z+2
     // stream into shared memory, and the loads of plane z overlap the
     // ingredients of z+1.  Stage buffers are indexed by zg & 1 (zg >= -1).
-    const int z1 = min(z0 + ZCH, P.nz);
-    auto fslot = [&](int zg) { return sphi + ((zg - z0 + 2 + 5 * ZCH) % 5) * G::P2; };
-    auto islot = [&](int zg) { return (zg - z0 + 1 + 3 * ZCH) % 3; };
+    // zg >= z0 - 2 for phi planes and zg >= z0 - 1 for ingredient planes
+    auto fslot = [&](int zg) { return sphi + ((unsigned)(zg - z0 + 2) % 5u) * G::P2; };
+    auto islot = [&](int zg) { return (int)((unsigned)(zg - z0 + 1) % 3u); };
 
     for (int zg = z0 - 2; zg <= z0 + 1; ++zg) async_phi_plane<L, G>(P, phi_n, fslot(zg), zg, halo);
     fetch_ring(z0 - 1);
@@ -791,10 +789,9 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
                                                    phi_np1, moment_out, st, macc);
     }
     cp_async_wait_all();
-    if (!IS_PHI && mass_partials) block_mass_out<G::NT>(macc, mass_partials, mass_slot);
 }
 
-template <class L, class SP, int BY, int ZCH, int BX = 32>
+template <class L, class SP, int BY, int BX = 32>
 constexpr size_t march_smem(bool is_phi) {
     using G = Geo<L, BY, BX>;
     using R = typename SP::real;
@@ -804,24 +801,33 @@ constexpr size_t march_smem(bool is_phi) {
 
 // ---- the two step kernels ----------------------------------------------------------
 
-template <class L, class SP, int BY, int ZCH, int MINB, bool WALLS, int BX = 32>
+// Block (bx, by, bz) marches the tile at (bx BX, by BY) over the planes
+// [bz zch, min((bz + 1) zch, nz)).
+template <class L, class SP, int BY, int MINB, bool WALLS, int BX = 32>
 __global__ void __launch_bounds__(BX * BY, MINB)
 k_phi_step(const KParams K, const typename SP::store_t* __restrict__ gin,
            typename SP::store_t* __restrict__ gout, const typename SP::real* __restrict__ phi_n,
-           const typename SP::real* __restrict__ c_n, typename SP::real* __restrict__ phi_np1) {
-    march<L, SP, BY, ZCH, true, WALLS, BX>(K, gin, gout, phi_n, nullptr, c_n, phi_np1, nullptr,
-                                       blockIdx.x * BX, blockIdx.y * BY, blockIdx.z * ZCH, 0);
+           const typename SP::real* __restrict__ c_n, typename SP::real* __restrict__ phi_np1, int zch) {
+    MassAcc<typename SP::real> macc{0, 0};
+    const int z0 = blockIdx.z * zch;
+    march<L, SP, BY, true, WALLS, BX>(K, gin, gout, phi_n, nullptr, c_n, phi_np1, macc, blockIdx.x * BX,
+                                      blockIdx.y * BY, z0, min(z0 + zch, K.P.nz));
 }
 
-template <class L, class SP, int BY, int ZCH, int MINB, bool WALLS, int BX = 32, class LH = L>
+template <class L, class SP, int BY, int MINB, bool WALLS, int BX = 32, class LH = L>
 __global__ void __launch_bounds__(BX * BY, MINB)
 k_c_step(const KParams K, const typename SP::store_t* __restrict__ hin,
          typename SP::store_t* __restrict__ hout, const typename SP::real* __restrict__ phi_n,
          const typename SP::real* __restrict__ phi_np1, const typename SP::real* __restrict__ c_n,
-         typename SP::real* __restrict__ c_np1, double* __restrict__ mass_partials) {
-    march<L, SP, BY, ZCH, false, WALLS, BX, long long, LH>(K, hin, hout, phi_n, phi_np1, c_n, c_np1, mass_partials,
-                                        blockIdx.x * BX, blockIdx.y * BY, blockIdx.z * ZCH,
-                                        blockIdx.x + gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z));
+         typename SP::real* __restrict__ c_np1, double* __restrict__ mass_partials, int zch) {
+    using G = Geo<L, BY, BX>;
+    MassAcc<typename SP::real> macc{0, 0};
+    const int z0 = blockIdx.z * zch;
+    march<L, SP, BY, false, WALLS, BX, long long, LH>(K, hin, hout, phi_n, phi_np1, c_n, c_np1, macc,
+                                                      blockIdx.x * BX, blockIdx.y * BY, z0, min(z0 + zch, K.P.nz));
+    if (mass_partials)
+        block_mass_out<G::NT>(macc, mass_partials,
+                              blockIdx.x + gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z));
 }
 
 // ---- initialisation -------------------------------------------------------------------
@@ -1031,7 +1037,9 @@ k_mass_corr_plan(const double* __restrict__ partials, int nblocks, MassCorr* __r
     if (threadIdx.x == 0) {
         const double dM = mc->target - sc;
         long long k = 0;
-        if (dM != 0.0) {
+        // a non-finite mass (a state that has blown up) corrects nothing: the
+        // node count stays within [0, N] whatever the partial sums hold
+        if (dM != 0.0 && isfinite(dM)) {
             const double want = fabs(dM) / delta_target;
             k = want < 1.0 ? 1 : (want > (double)N ? N : (long long)llrint(want));
         }

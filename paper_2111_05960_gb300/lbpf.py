@@ -17,9 +17,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgb_lbpf.so")
 
-LBPF_OK, LBPF_EINVAL, LBPF_ENOMEM, LBPF_ECUDA, LBPF_EUNSTABLE, LBPF_ETIMEOUT, LBPF_ESTATE, \
-    LBPF_EUNSUPPORTED = range(8)
-STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EUNSTABLE", "ETIMEOUT", "ESTATE", "EUNSUPPORTED"]
+LBPF_OK, LBPF_EINVAL, LBPF_ENOMEM, LBPF_ECUDA, LBPF_EUNSTABLE = range(5)
+LBPF_ESTATE, LBPF_EUNSUPPORTED = 6, 7          # 5 is unused (no call times out)
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EUNSTABLE", "(unused)", "ESTATE", "EUNSUPPORTED"]
 LBPF_D2Q9, LBPF_D3Q19, LBPF_D2Q5, LBPF_D3Q7 = 0, 1, 2, 3
 LBPF_FP64, LBPF_FP32, LBPF_FP32_BF16DEV, LBPF_FP32_FP16DEV = 0, 1, 2, 3
 PRECISIONS = {"fp64": LBPF_FP64, "fp32": LBPF_FP32, "bf16dev": LBPF_FP32_BF16DEV,
@@ -230,13 +230,35 @@ def lbpf_batch_set_tile(ctx, tile_x: int, tile_rows: int) -> None:
 NOALLOC_MAX_ELEMENTS = 67108864
 
 
+def _stream_handle(cuda_stream):
+    """A cudaStream_t address from None, an int or a torch.cuda.Stream."""
+    if cuda_stream is None:
+        return None
+    if hasattr(cuda_stream, "cuda_stream"):
+        return cuda_stream.cuda_stream or None
+    return int(cuda_stream) or None
+
+
 def lbpf_mass_noalloc(c_dev, phi_dev, n: int, precision: int, out_dev, cuda_stream=None) -> None:
     """Sums of c and phi over caller-owned device arrays into out_dev (3 doubles on
-    the device), with no allocation; see include/lbpf.h.  Queued on cuda_stream."""
-    cp = c_dev.data_ptr() if hasattr(c_dev, "data_ptr") else int(c_dev)
-    pp = phi_dev.data_ptr() if hasattr(phi_dev, "data_ptr") else int(phi_dev)
-    op = out_dev.data_ptr() if hasattr(out_dev, "data_ptr") else int(out_dev)
-    _check(load().lbpf_mass_noalloc(cp, pp, int(n), int(precision), op, cuda_stream or None))
+    the device), with no allocation; see include/lbpf.h.  Queued on cuda_stream
+    (None, a cudaStream_t address or a torch.cuda.Stream).  c_dev, phi_dev: CUDA
+    tensors, contiguous, float64 for LBPF_FP64 or float32 for LBPF_FP32, with at
+    least n elements; out_dev: a contiguous CUDA float64 tensor of >= 3 elements."""
+    import torch
+    want = {LBPF_FP64: torch.float64, LBPF_FP32: torch.float32}.get(int(precision))
+    for name, t in (("c", c_dev), ("phi", phi_dev)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+            raise ValueError("%s must be a contiguous CUDA tensor" % name)
+        if want is not None and t.dtype != want:
+            raise ValueError("%s has dtype %s; precision %d needs %s" % (name, t.dtype, precision, want))
+        if t.numel() < max(int(n), 0):
+            raise ValueError("%s has %d elements, fewer than n = %d" % (name, t.numel(), n))
+    if not (isinstance(out_dev, torch.Tensor) and out_dev.is_cuda and out_dev.is_contiguous()
+            and out_dev.dtype == torch.float64 and out_dev.numel() >= 3):
+        raise ValueError("out_dev must be a contiguous CUDA float64 tensor of at least 3 elements")
+    _check(load().lbpf_mass_noalloc(c_dev.data_ptr(), phi_dev.data_ptr(), int(n), int(precision),
+                                    out_dev.data_ptr(), _stream_handle(cuda_stream)))
 
 
 ADJ_PARAM_NAMES = ("D_l", "tau_g", "tau_h", "lam", "a_at", "D_s")

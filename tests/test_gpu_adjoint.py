@@ -237,7 +237,8 @@ def test_adjoint_needs_recording():
     assert ei.value.status == L.LBPF_EUNSUPPORTED
 
 
-def test_autograd_function_solid_fraction_loss():
+@pytest.mark.parametrize("theta_device", ["cpu", "cuda:0"])
+def test_autograd_function_solid_fraction_loss(theta_device):
     import torch
     from paper_2111_05960_gb300 import autograd as AG
     m, phi0, c0, target_np = _porous(16)
@@ -251,9 +252,11 @@ def test_autograd_function_solid_fraction_loss():
         return ((s - target) ** 2).sum()
 
     phi0_t = torch.tensor(phi0, device=dev, requires_grad=True)
-    theta = torch.tensor([m.D_l, m.tau_g, m.tau_h, m.lam], dtype=torch.float64, requires_grad=True)
+    theta = torch.tensor([m.D_l, m.tau_g, m.tau_h, m.lam], dtype=torch.float64, device=theta_device,
+                         requires_grad=True)
     loss = loss_of(phi0_t, theta)
     loss.backward()
+    assert theta.grad.device == theta.device
     base = theta.detach()
     for i in range(4):
         def f(d, i=i):
@@ -273,3 +276,46 @@ def test_autograd_function_solid_fraction_loss():
     rich, fd = _richardson(g, 1e-4)
     ad = float((phi0_t.grad * dphi).sum())
     assert abs(ad - rich) <= 1e-6 * abs(rich), (ad, rich, fd)
+
+
+def test_differentiable_workload_as_configured_2000_steps():
+    """The differentiable 3-D workload as configured: 128^3 porous medium
+    (porosity 0.4), 2000 FP32 steps with the FP64 mass correction, a checkpoint
+    every 100 steps, the slab solid-fraction loss.  The same trajectory in FP64
+    gives the reference: its adjoint is pinned to the oracle's FP64 discrete
+    adjoint by the tests above, and here it is checked against central
+    differences (h = 1e-4, Richardson-extrapolated) of the FP64 GPU forward over
+    the same 2000 steps, for dL/dD_l, dL/dM_phi = 3 dL/dtau_g (tau_h held) and
+    one unit direction of phi0.  The FP32 adjoint is then compared with the FP64
+    one."""
+    import dataclasses
+    m, phi0, c0, target = WL.differentiable_3d(128)
+    T, K = 2000, 100
+    res = {}
+    for prec, me in (("fp32", 1), ("fp64", 0)):
+        sim = L.Simulation(m, phi0, c0, precision=prec, checkpoint_every=K, mass_every=me)
+        sim.step(T)
+        loss, seed = _slab_loss(sim.fields()[0], target)
+        res[prec] = (loss,) + tuple(sim.adjoint(seed, None))
+        sim.close()
+    loss64, d64, _, p64 = res["fp64"]
+    loss32, d32, _, p32 = res["fp32"]
+    h = 1e-4
+    rich_D, fd_D = _richardson(lambda d: _final_loss(dataclasses.replace(m, D_l=m.D_l + d), phi0, c0, T, target), h)
+    rich_M, fd_M = _richardson(
+        lambda d: _final_loss(dataclasses.replace(m, tau_g=m.tau_g + 3.0 * d), phi0, c0, T, target), h)
+    dphi = np.random.default_rng(11).standard_normal(m.shape)
+    dphi /= np.linalg.norm(dphi)
+    rich_p, fd_p = _richardson(lambda d: _final_loss(m, phi0 + d * dphi, c0, T, target), h)
+    ad_D, ad_M, ad_p = p64[0], 3.0 * p64[1], float(np.vdot(d64, dphi))
+    print("loss fp64 %.10e fp32 %.10e" % (loss64, loss32))
+    print("dL/dD_l   adjoint %.10e  richardson %.10e  central %.10e" % (ad_D, rich_D, fd_D))
+    print("dL/dM_phi adjoint %.10e  richardson %.10e  central %.10e" % (ad_M, rich_M, fd_M))
+    print("dphi0     adjoint %.10e  richardson %.10e  central %.10e" % (ad_p, rich_p, fd_p))
+    assert abs(ad_D - rich_D) <= 1e-5 * abs(rich_D), (ad_D, rich_D, fd_D)
+    assert abs(ad_M - rich_M) <= 1e-5 * abs(rich_M), (ad_M, rich_M, fd_M)
+    assert abs(ad_p - rich_p) <= 1e-5 * abs(rich_p), (ad_p, rich_p, fd_p)
+    e_field = rel_err(d32, d64)
+    e_par = np.max(np.abs(p32[:4] - p64[:4]) / np.maximum(np.abs(p64[:4]), 1e-300))
+    print("fp32 vs fp64 adjoint: dphi0 %.3e  params %.3e  loss %.3e" % (e_field, e_par, abs(loss32 - loss64) / loss64))
+    assert e_field < 1e-2 and e_par < 1e-2, (e_field, e_par)

@@ -44,9 +44,13 @@ def test_noalloc_sums_match_lbpf_mass_on_two_calls(precision):
     prec = L.LBPF_FP64 if precision == "fp64" else L.LBPF_FP32
 
     out = torch.full((3,), float("nan"), dtype=torch.float64, device="cuda")
-    for _ in range(2):
+    side = torch.cuda.Stream()
+    # two calls in a row on the legacy default stream, then two on a caller's
+    # stream handed over as a torch.cuda.Stream
+    for stream in (None, None, side, side):
         out.fill_(float("nan"))
-        L.lbpf_mass_noalloc(c, phi, c.numel(), prec, out)
+        torch.cuda.synchronize()
+        L.lbpf_mass_noalloc(c, phi, c.numel(), prec, out, stream)
         torch.cuda.synchronize()
         got = out.cpu().numpy()
         assert abs(got[0] - mc) <= MASS_TOL * abs(mc)
@@ -58,9 +62,11 @@ def test_noalloc_rejects_oversize_and_bad_arguments():
     import torch
     out = torch.zeros(3, dtype=torch.float64, device="cuda")
     a = torch.zeros(8, dtype=torch.float64, device="cuda")
-    with pytest.raises(L.LbpfError) as ei:
-        L.lbpf_mass_noalloc(a, a, L.NOALLOC_MAX_ELEMENTS + 1, L.LBPF_FP64, out)
-    assert ei.value.status == L.LBPF_EINVAL and "no-alloc maximum" in str(ei.value)
+    # the C entry point itself rejects n above its maximum before touching any
+    # buffer (called raw: the binding would refuse n > numel first)
+    st = L.load().lbpf_mass_noalloc(a.data_ptr(), a.data_ptr(), L.NOALLOC_MAX_ELEMENTS + 1, L.LBPF_FP64,
+                                    out.data_ptr(), None)
+    assert st == L.LBPF_EINVAL and "no-alloc maximum" in L.lbpf_last_error(None)
     with pytest.raises(L.LbpfError):
         L.lbpf_mass_noalloc(a, a, 8, L.LBPF_FP32_FP16DEV, out)
     with pytest.raises(L.LbpfError):
@@ -68,5 +74,25 @@ def test_noalloc_rejects_oversize_and_bad_arguments():
     # n = 0 writes zero sums
     out.fill_(1.0)
     L.lbpf_mass_noalloc(a, a, 0, L.LBPF_FP64, out)
+    torch.cuda.synchronize()
+    assert np.all(out.cpu().numpy() == 0.0)
+
+
+def test_noalloc_binding_checks_its_arguments():
+    """The binding refuses buffers the kernels would misread: host tensors, a
+    dtype other than the precision's, fewer than n elements, a short output."""
+    import torch
+    out = torch.zeros(3, dtype=torch.float64, device="cuda")
+    a64 = torch.zeros(8, dtype=torch.float64, device="cuda")
+    a32 = torch.zeros(8, dtype=torch.float32, device="cuda")
+    with pytest.raises(ValueError):
+        L.lbpf_mass_noalloc(a32, a32, 8, L.LBPF_FP64, out)
+    with pytest.raises(ValueError):
+        L.lbpf_mass_noalloc(a64.cpu(), a64, 8, L.LBPF_FP64, out)
+    with pytest.raises(ValueError):
+        L.lbpf_mass_noalloc(a64, a64, 9, L.LBPF_FP64, out)
+    with pytest.raises(ValueError):
+        L.lbpf_mass_noalloc(a64, a64, 8, L.LBPF_FP64, out[:2])
+    L.lbpf_mass_noalloc(a32, a32, 8, L.LBPF_FP32, out)
     torch.cuda.synchronize()
     assert np.all(out.cpu().numpy() == 0.0)
