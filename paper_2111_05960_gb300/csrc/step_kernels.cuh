@@ -316,6 +316,7 @@ struct Geo {
     static constexpr int NPHI = (L::D == 3) ? 5 : 1; // phi planes in the window
     static constexpr int NING = (L::D == 3) ? 3 : 1; // ingredient planes in the window
     static constexpr int NT = BX * BY;
+    __device__ static __forceinline__ int tid() { return threadIdx.x + BX * threadIdx.y; }
 };
 
 // Wrap (periodic) or mirror (wall) an index that is at most one node outside.
@@ -351,7 +352,7 @@ struct HaloOffsets {
     int o1[IT1];
     int c2[IT1];
     __device__ __forceinline__ void init(const StepParams& P, int x0, int y0, bool inside2, bool inside1) {
-        const int tid = threadIdx.x + G::BX * threadIdx.y;
+        const int tid = G::tid();
 #pragma unroll
         for (int it = 0; it < IT2; ++it) {
             const int s = tid + it * G::NT;
@@ -383,7 +384,7 @@ struct HaloOffsets {
 template <class L, class G, typename R>
 __device__ __forceinline__ void async_phi_plane(const StepParams& P, const R* __restrict__ phi, R* dst, int zg,
                                                 const HaloOffsets<G>& H) {
-    const int tid = threadIdx.x + G::BX * threadIdx.y;
+    const int tid = G::tid();
     const int gz = (L::D == 3) ? map_coord(zg, P.nz, P.bc[2]) : 0;
     const R* src = phi + (long long)gz * P.nx * P.ny;
 #pragma unroll
@@ -395,7 +396,7 @@ __device__ __forceinline__ void async_phi_plane(const StepParams& P, const R* __
 template <class L, class G, typename R>
 __device__ __forceinline__ void async_ring(const StepParams& P, const R* __restrict__ f, R* dst, int zg,
                                            const HaloOffsets<G>& H) {
-    const int tid = threadIdx.x + G::BX * threadIdx.y;
+    const int tid = G::tid();
     const int gz = (L::D == 3) ? map_coord(zg, P.nz, P.bc[2]) : 0;
     const R* src = f + (long long)gz * P.nx * P.ny;
 #pragma unroll
@@ -406,10 +407,9 @@ __device__ __forceinline__ void async_ring(const StepParams& P, const R* __restr
 // grad(phi) by directional derivatives (Eq. DerivDirec_Grad, Eq. Grad) at offset c
 // of the plane p0, with pm / pp the planes below / above.  Opposite links give
 // the same term, so each pair is counted once, doubled.
-template <class L, int BY, int BX, typename R>
+template <class L, class G, typename R>
 __device__ __forceinline__ void plane_gradient(const R* pm, const R* p0, const R* pp, int c,
                                                R& gx, R& gy, R& gz) {
-    using G = Geo<L, BY, BX>;
     gx = gy = gz = R(0);
 #pragma unroll
     for (int k = 1; k < L::Q; ++k) {
@@ -432,12 +432,11 @@ __device__ __forceinline__ void plane_gradient(const R* pm, const R* p0, const R
 
 // Ingredients of the phi collision on one plane: alpha_g, beta_g (x, y, z) and
 // A = G^st + G^dw.
-template <class L, int BY, int BX, bool U, typename R>
+template <class L, class G, bool U, typename R>
 __device__ __forceinline__ void phi_ingredients(const StepParams& P, const Coef<R>& C, const R* cst,
                                                 const R* pm, const R* p0, const R* pp, V4<R>* ing, R* sA,
-                                                const HaloOffsets<Geo<L, BY, BX>>& H) {
-    using G = Geo<L, BY, BX>;
-    const int tid = threadIdx.x + G::BX * threadIdx.y;
+                                                const HaloOffsets<G>& H) {
+    const int tid = G::tid();
     const R half_src = R(1) - R(0.5) * C.omg;
     constexpr int IT = (G::P1 + G::NT - 1) / G::NT;
 #pragma unroll
@@ -452,7 +451,7 @@ __device__ __forceinline__ void phi_ingredients(const StepParams& P, const Coef<
         v.a = div36(C.omg * ph + half_src * A);         // per unit m_k (w_k = m_k / 36)
         if (P.counter_term) {
             R gx, gy, gz_;
-            plane_gradient<L, BY, BX>(pm, p0, pp, c2, gx, gy, gz_);
+            plane_gradient<L, G>(pm, p0, pp, c2, gx, gy, gz_);
             const R inv = rsqrt_reg<R>(gx * gx + gy * gy + gz_ * gz_, C.eps2);
             const R k = C.kct36 * ph * (R(1) - ph) * inv;   // (4/W) phi (1 - phi) n, per unit m_k
             v.b = k * gx; v.c = k * gy; v.d = k * gz_;
@@ -466,12 +465,11 @@ __device__ __forceinline__ void phi_ingredients(const StepParams& P, const Coef<
 
 // Ingredients of the h collision on one plane: P = gamma D mu and
 // beta_h = (1 - w_h/2) gamma (mu D' grad phi + j_at).
-template <class L, class LH, int BY, int BX, bool U, typename R>
+template <class L, class LH, class G, bool U, typename R>
 __device__ __forceinline__ void c_ingredients(const StepParams& P, const Coef<R>& C, const R* cst, const R* pst,
                                               const R* pm, const R* p0, const R* pp, V4<R>* ing,
-                                              const HaloOffsets<Geo<L, BY, BX>>& H) {
-    using G = Geo<L, BY, BX>;
-    const int tid = threadIdx.x + G::BX * threadIdx.y;
+                                              const HaloOffsets<G>& H) {
+    const int tid = G::tid();
     constexpr int IT = (G::P1 + G::NT - 1) / G::NT;
 #pragma unroll
     for (int it = 0; it < IT; ++it) {
@@ -482,7 +480,7 @@ __device__ __forceinline__ void c_ingredients(const StepParams& P, const Coef<R>
         const R dphi = pst[s] - ph;                        // explicit Euler dphi/dt
         const R mu = closure_mu<U>(C, ph, cst[s]);
         R gx, gy, gz_;
-        plane_gradient<L, BY, BX>(pm, p0, pp, c2, gx, gy, gz_);
+        plane_gradient<L, G>(pm, p0, pp, c2, gx, gy, gz_);
         const R inv = rsqrt_reg<R>(gx * gx + gy * gy + gz_ * gz_, C.eps2);
         const R f = mu * C.Dp + at_coef<U>(C, mu) * dphi * inv;   // F = (mu D' + j_at / |grad|) grad
         V4<R> v;
@@ -739,11 +737,11 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
     auto ingredients = [&](int slot_i, const R* pm, const R* p0, const R* pp, int zg) {
         const int b = zg & 1;
         if (IS_PHI)
-            phi_ingredients<L, BY, BX, U>(P, C, cst + b * G::P1, pm, p0, pp, sing + slot_i * G::P1,
-                                          sA + slot_i * G::P1, halo);
+            phi_ingredients<L, G, U>(P, C, cst + b * G::P1, pm, p0, pp, sing + slot_i * G::P1,
+                                     sA + slot_i * G::P1, halo);
         else
-            c_ingredients<L, LH, BY, BX, U>(P, C, cst + b * G::P1, pst + b * G::P1, pm, p0, pp,
-                                            sing + slot_i * G::P1, halo);
+            c_ingredients<L, LH, G, U>(P, C, cst + b * G::P1, pst + b * G::P1, pm, p0, pp,
+                                       sing + slot_i * G::P1, halo);
     };
 
     static_assert(L::D == 3, "2-D domains march through the D2Q9R view");

@@ -306,16 +306,20 @@ def _crop(n, bc=(1, 1, 1), **kw):
     return mc, np.ascontiguousarray(phi0[:n, :n, :n]), np.ascontiguousarray(c0[:n, :n, :n])
 
 
+@pytest.mark.parametrize("eps_n", [1e-12, 1e-6])
 @pytest.mark.parametrize("source", ["periodic_24", "crop_24_walls"])
-def test_fp64_porous_medium_default_eps_matches_oracle(source):
+def test_fp64_porous_medium_matches_oracle(source, eps_n):
     """The benchmark's scheme in FP64 (D3Q19, D_s = 0 with the anti-trapping
-    current at a = 1/4, counter term on, lambda*, eps_n = 1e-12) on a 24^3 porous
-    medium, 100 steps, every field and population plane within 1e-11."""
+    current at a = 1/4, counter term on, lambda*) on a 24^3 porous medium, with
+    the library's default eps_n = 1e-12 and the workload's 1e-6, 100 steps, every
+    field and population plane within 1e-11."""
+    import dataclasses
     if source == "periodic_24":
         m, phi0, c0 = WL.porous_3d(n=24)
     else:
         m, phi0, c0 = _crop(24)
-    assert m.D_s == 0.0 and m.anti_trapping == 1 and m.eps_n == 1e-12
+    m = dataclasses.replace(m, eps_n=eps_n)
+    assert m.D_s == 0.0 and m.anti_trapping == 1
     sim = L.Simulation(m, phi0, c0, precision="fp64")
     sim.step(100)
     phi, c, mu = sim.fields()
@@ -329,16 +333,13 @@ def test_fp64_porous_medium_default_eps_matches_oracle(source):
     assert max(errs.values()) < FP64_TOL, errs
 
 
-@pytest.mark.parametrize("eps_n", [1e-3, 1e-12])
+@pytest.mark.parametrize("eps_n", [1e-6, 1e-3])
 def test_fp32_bench_tile_on_porous_crop_150_steps(eps_n):
-    """FP32 in the benchmark's launch configuration (32 x 4 tiles marching along
-    z, the composition kernel with the FP64 mass correction every step) on a 64^3
-    corner crop of the benchmark medium closed by walls, 150 steps, against the
-    FP64 oracle.  With eps_n = 1e-3 every node is within the 2e-5 target.  With
-    eps_n = 1e-12 the unit normal turns freely at the few nodes where grad phi
-    vanishes inside the interface (thin necks, saddles) and rounding differences
-    there are amplified; the 99.9th percentile of the error stays within 2e-5 and
-    the maximum is stated below."""
+    """FP32 in the benchmark's launch configuration (the step kernels of the
+    256^3 run, the composition kernel with the FP64 mass correction every step)
+    on a 64^3 corner crop of the benchmark medium closed by walls, 150 steps,
+    against the FP64 oracle: every node of phi and c within the 2e-5 target, with
+    the workload's eps_n = 1e-6 and with 1e-3."""
     m, phi0, c0 = _crop(64, eps_n=eps_n)
     o = O.Oracle(to_oracle(m), phi0, c0).step(150)
     sim = L.Simulation(m, phi0, c0, precision="fp32", mass_every=1)
@@ -346,11 +347,25 @@ def test_fp32_bench_tile_on_porous_crop_150_steps(eps_n):
     phi, c, _ = sim.fields()
     sim.close()
     errs = dict(phi=rel_err(phi, o.phi), c=rel_err(c, o.c))
-    p999 = {k: float(np.quantile(np.abs(a - b), 0.999) / np.abs(b).max())
-            for k, a, b in (("phi", phi, o.phi), ("c", c, o.c))}
-    print(eps_n, errs, p999)
-    if eps_n == 1e-3:
-        assert max(errs.values()) < 2e-5, errs
-    else:
-        assert max(p999.values()) < 2e-5, p999
-        assert max(errs.values()) < 1e-3, errs
+    print(eps_n, errs)
+    assert max(errs.values()) < 2e-5, errs
+
+
+def test_fp32_with_unregularised_normal_departs_only_in_flat_bulk():
+    """With eps_n = 1e-12 the unit normal is undefined where grad phi is only
+    rounding (the flat bulk that the clipped signed distance leaves), and FP32
+    and FP64 pick different directions there.  Every node where FP32 then
+    misses 2e-5 lies in that bulk (phi within 1e-3 of 0 or 1), none on an
+    interface."""
+    m, phi0, c0 = _crop(64, eps_n=1e-12)
+    o = O.Oracle(to_oracle(m), phi0, c0).step(150)
+    sim = L.Simulation(m, phi0, c0, precision="fp32", mass_every=1)
+    sim.step(150)
+    phi, c, _ = sim.fields()
+    sim.close()
+    e = np.maximum(np.abs(phi - o.phi) / np.abs(o.phi).max(), np.abs(c - o.c) / np.abs(o.c).max())
+    bad = e > 2e-5
+    bulk = (o.phi < 1e-3) | (o.phi > 1.0 - 1e-3)
+    print("max %.2e, %d nodes above 2e-5" % (e.max(), bad.sum()))
+    assert np.all(bulk[bad]), o.phi[bad & ~bulk][:10]
+    assert np.quantile(e[~bulk], 1.0) < 2e-5

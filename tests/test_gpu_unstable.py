@@ -55,3 +55,41 @@ def test_the_same_medium_with_three_node_interfaces_stays_stable():
     sim.close()
     assert np.all(np.isfinite(phi)) and np.all(np.isfinite(c))
     assert phi.min() > -1e-3 and phi.max() < 1.0 + 1e-3
+
+
+def test_injected_allocation_failure_reports_enomem_and_leaks_nothing(monkeypatch):
+    """LBPF_FAULT=alloc makes the library's device allocations fail on the host
+    side (no GPU fault): lbpf_create returns LBPF_ENOMEM, hands back no context
+    and leaves device memory as it found it; without the variable the same call
+    succeeds."""
+    import torch
+    m, phi0, c0 = WL.porous_3d(n=16)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    monkeypatch.setenv("LBPF_FAULT", "alloc")
+    with pytest.raises(L.LbpfError) as ei:
+        L.Simulation(m, phi0, c0, precision="fp32", mass_every=1)
+    assert ei.value.status == L.LBPF_ENOMEM
+    assert "injected allocation failure" in str(ei.value)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    monkeypatch.delenv("LBPF_FAULT")
+    sim = L.Simulation(m, phi0, c0, precision="fp32", mass_every=1)
+    sim.step(3)
+    sim.close()
+
+
+def test_non_finite_initial_field_is_reported_on_the_first_mass_call():
+    """A NaN seeded into phi0 on the host propagates through the initialisation;
+    the first lbpf_mass reports LBPF_EUNSTABLE."""
+    m, phi0, c0 = WL.porous_3d(n=16)
+    phi0 = phi0.copy()
+    phi0[3, 4, 5] = float("nan")
+    sim = L.Simulation(m, phi0, c0, precision="fp64")
+    with pytest.raises(L.LbpfError) as ei:
+        sim.mass()
+    assert ei.value.status == L.LBPF_EUNSTABLE
+    with pytest.raises(L.LbpfError) as ei:
+        sim.step(1)
+    assert ei.value.status == L.LBPF_ESTATE
+    sim.close()
