@@ -37,6 +37,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=256, help="side of the cubic domain")
+    ap.add_argument("--nz", type=int, default=0, help="planes along z (0: n, a cube); for small profiling cases")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16dev", "bf16dev"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -204,15 +205,16 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_workload(n):
+def make_workload(n, nz=0):
     from paper_2111_05960_gb300 import workloads as WL
-    return WL.porous_3d(n=n)
+    return WL.porous_3d(n=n, nz=nz or None)
 
 
 def workload_config(model):
     """The workload both arms run, by what it is (the same dict for the GPU arm
     and the oracle arm; the arithmetic type is the line's dtype)."""
-    return {"workload": "porous_3d_%d_d3q19" % model.nx, "nodes": model.nodes, "lattice": "D3Q19",
+    size = "%d" % model.nx if model.nz == model.nx else "%dx%dx%d" % (model.nx, model.ny, model.nz)
+    return {"workload": "porous_3d_%s_d3q19" % size, "nodes": model.nodes, "lattice": "D3Q19",
             "porosity": 0.35, "W": model.W, "D_l": model.D_l, "D_s": model.D_s,
             "counter_term": model.counter_term, "anti_trapping": model.anti_trapping,
             "boundaries": "periodic", "inputs": "seeded Gaussian-random-field medium (PCG64 seed 0)"}
@@ -450,7 +452,7 @@ def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
         return
-    model, phi0, c0 = make_workload(args.n)
+    model, phi0, c0 = make_workload(args.n, args.nz)
     import oracle as O
     O.build()
     names = O.OracleParams.__dataclass_fields__
@@ -519,7 +521,7 @@ def run_ours(args):
     B.build()
     L.load()
 
-    model, phi0, c0 = make_workload(args.n)
+    model, phi0, c0 = make_workload(args.n, args.nz)
     N = model.nodes
     stream = torch.cuda.Stream()
     prec = args.precision

@@ -107,6 +107,9 @@ struct BatchImpl {
     }
 };
 
+// Row pitch of a batch instance: nx rounded up to 8 elements.
+int row_pitch(int nx) { return (nx + 7) & ~7; }
+
 const BatchDispatch* pick_batch(int precision) {
     switch (precision) {
         case LBPF_FP64: return BatchImpl<StoreF64>::table();
@@ -210,9 +213,10 @@ lbpf_status lbpf_create_batch(const lbpf_params* p, int32_t n, const double* con
         if (validate(&p[i], why) != LBPF_OK) return fail(nullptr, LBPF_EINVAL, "instance " + std::to_string(i) + ": " + why);
         if (p[i].lattice != LBPF_D2Q9) return fail(nullptr, LBPF_EUNSUPPORTED, "batches hold 2-D D2Q9 instances");
         const long long sb = p[i].precision == LBPF_FP64 ? 8 : (p[i].precision == LBPF_FP32 ? 4 : 2);
-        if (9LL * p[i].nx * p[i].ny * sb >= (1LL << 31))
+        if (9LL * row_pitch(p[i].nx) * p[i].ny * sb >= (1LL << 31))
             return fail(nullptr, LBPF_EINVAL,
-                        "instance " + std::to_string(i) + ": 9 nx ny x bytes per value must stay below 2^31");
+                        "instance " + std::to_string(i) +
+                            ": 9 ny x (nx rounded up to 8) x bytes per value must stay below 2^31");
         if (p[i].precision != p[0].precision) return fail(nullptr, LBPF_EINVAL, "all instances need one precision");
         if (p[i].mass_every != 0) return fail(nullptr, LBPF_EUNSUPPORTED, "mass correction is not built for batches");
         if (p[i].checkpoint_every != 0) return fail(nullptr, LBPF_EUNSUPPORTED, "the adjoint is not built for batches");
@@ -240,13 +244,19 @@ lbpf_status lbpf_create_batch(const lbpf_params* p, int32_t n, const double* con
         return st;
     };
     // instance table: offsets into the concatenated buffers (the tile list
-    // follows the tile shape, set below)
-    long long nodes = 0;
+    // follows the tile shape, set below).  Each instance keeps its rows at a
+    // pitch of nx rounded up to 8 elements, so that every row and every
+    // instance starts on a 32-byte sector in FP32 (the padding is zero in the
+    // fields and never read by the pulls).
+    long long nodes = 0;          // stored elements per field, padding included
+    std::vector<long long> dense_off;
     try {
         ctx->binst.resize(n);
+        dense_off.resize(n);
+        long long dense = 0;
         for (int i = 0; i < n; ++i) {
             BatchInst& I = ctx->binst[i];
-            I.K = make_kparams(&p[i]);
+            I.K = make_kparams(&p[i], row_pitch(p[i].nx));
             I.Km = march_kparams(I.K, LBPF_D2Q9);
             I.fld_off = nodes;
             I.pop_off = 9 * nodes;
@@ -254,7 +264,9 @@ lbpf_status lbpf_create_batch(const lbpf_params* p, int32_t n, const double* con
             I.tile_begin = 0;
             I.walls = (p[i].bc[0] || p[i].bc[1]) ? 1 : 0;
             I.pad = 0;
-            nodes += I.K.P.N;
+            dense_off[i] = dense;
+            nodes += I.K.P.NS;
+            dense += I.K.P.N;
         }
     } catch (...) {
         return abort_create(fail(ctx, LBPF_ENOMEM, "host allocation failed"));
@@ -283,6 +295,12 @@ lbpf_status lbpf_create_batch(const lbpf_params* p, int32_t n, const double* con
     ctx->mass_blocks = (int)std::max<long long>(1, std::min<long long>((nodes + kMassThreads - 1) / kMassThreads, 4LL * sms));
     if ((st = alloc(ctx, (void**)&ctx->partials, sizeof(double) * 3 * ctx->mass_blocks, "mass partials")) != LBPF_OK) return abort_create(st);
     if ((st = alloc(ctx, (void**)&ctx->mass_out, sizeof(double) * 3, "mass result")) != LBPF_OK) return abort_create(st);
+    // the row padding of both field sets stays zero (lbpf_mass sums every element)
+    for (int i = 0; i < 2; ++i) {
+        e = cudaMemsetAsync(ctx->phi[i], 0, ctx->real_size * N, ctx->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(ctx->c[i], 0, ctx->real_size * N, ctx->stream);
+        if (e != cudaSuccess) { cuda_fail(ctx, e, "clearing the fields"); return abort_create(LBPF_ECUDA); }
+    }
 
     // fields: per instance into the staging buffer (host) or straight from the caller (device)
     if (!ptr_is_device) {
@@ -291,22 +309,25 @@ lbpf_status lbpf_create_batch(const lbpf_params* p, int32_t n, const double* con
     for (int i = 0; i < n; ++i) {
         const BatchInst& I = ctx->binst[i];
         const size_t Ni = (size_t)I.K.P.N;
+        const int nx = I.K.P.nx, sx = I.K.P.sx;
         const double* sphi = phi0[i];
         const double* sc = c0[i];
         if (!ptr_is_device) {
-            e = cudaMemcpyAsync(ctx->staging + I.fld_off, phi0[i], sizeof(double) * Ni, cudaMemcpyHostToDevice, ctx->stream);
+            e = cudaMemcpyAsync(ctx->staging + dense_off[i], phi0[i], sizeof(double) * Ni, cudaMemcpyHostToDevice,
+                                ctx->stream);
             if (e == cudaSuccess)
-                e = cudaMemcpyAsync(ctx->staging + N + I.fld_off, c0[i], sizeof(double) * Ni, cudaMemcpyHostToDevice, ctx->stream);
+                e = cudaMemcpyAsync(ctx->staging + N + dense_off[i], c0[i], sizeof(double) * Ni,
+                                    cudaMemcpyHostToDevice, ctx->stream);
             if (e != cudaSuccess) { cuda_fail(ctx, e, "copy of phi0/c0"); return abort_create(LBPF_ECUDA); }
-            sphi = ctx->staging + I.fld_off;
-            sc = ctx->staging + N + I.fld_off;
+            sphi = ctx->staging + dense_off[i];
+            sc = ctx->staging + N + dense_off[i];
         }
         if (is_f64(ctx)) {
-            launch_from_f64<double>(sphi, (double*)ctx->phi[0] + I.fld_off, (long long)Ni, ctx->stream);
-            launch_from_f64<double>(sc, (double*)ctx->c[0] + I.fld_off, (long long)Ni, ctx->stream);
+            launch_from_f64_rows<double>(sphi, (double*)ctx->phi[0] + I.fld_off, (long long)Ni, nx, sx, ctx->stream);
+            launch_from_f64_rows<double>(sc, (double*)ctx->c[0] + I.fld_off, (long long)Ni, nx, sx, ctx->stream);
         } else {
-            launch_from_f64<float>(sphi, (float*)ctx->phi[0] + I.fld_off, (long long)Ni, ctx->stream);
-            launch_from_f64<float>(sc, (float*)ctx->c[0] + I.fld_off, (long long)Ni, ctx->stream);
+            launch_from_f64_rows<float>(sphi, (float*)ctx->phi[0] + I.fld_off, (long long)Ni, nx, sx, ctx->stream);
+            launch_from_f64_rows<float>(sc, (float*)ctx->c[0] + I.fld_off, (long long)Ni, nx, sx, ctx->stream);
         }
     }
     ctx->cur = 0;

@@ -120,7 +120,7 @@ lbpf_status ensure_staging(lbpf_ctx* ctx);
 
 lbpf_status validate(const lbpf_params* p, std::string& why);
 lbpf::StepParams lattice_units(const lbpf_params* p);
-lbpf::KParams make_kparams(const lbpf_params* p);
+lbpf::KParams make_kparams(const lbpf_params* p, int sx = 0);
 lbpf::KParams march_kparams(const lbpf::KParams& kp, int lattice);
 void free_all(lbpf_ctx* ctx);
 void set_thread_error(const std::string& msg);
@@ -131,6 +131,11 @@ inline bool is_f64(const lbpf_ctx* ctx) { return ctx->p.precision == LBPF_FP64; 
 template <typename R>
 void launch_from_f64(const double* src, void* dst, long long n, cudaStream_t s) {
     lbpf::k_from_f64<R><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, (R*)dst, n);
+}
+// the same into rows of pitch sx (n values in rows of nx)
+template <typename R>
+void launch_from_f64_rows(const double* src, void* dst, long long n, int nx, int sx, cudaStream_t s) {
+    lbpf::k_from_f64_rows<R><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, (R*)dst, n, nx, sx);
 }
 
 // adjoint.cu

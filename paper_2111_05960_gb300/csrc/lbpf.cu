@@ -309,6 +309,9 @@ StepParams lbpf_rt::lattice_units(const lbpf_params* p) {
     for (int a = 0; a < 3; ++a) s.bc[a] = p->bc[a];
     if (p->lattice == LBPF_D2Q9) s.bc[2] = LBPF_PERIODIC;
     s.N = (long long)p->nx * p->ny * p->nz;
+    s.sx = p->nx;
+    s.sxy = (long long)p->nx * p->ny;
+    s.NS = s.N;
     s.omg = 1.0 / (p->tau_g + 0.5);
     s.omh = 1.0 / (p->tau_h + 0.5);
     s.M = p->tau_g / 3.0;
@@ -337,23 +340,29 @@ StepParams lbpf_rt::lattice_units(const lbpf_params* p) {
     return s;
 }
 
-// Geometry, coefficients (FP64 and FP32) and link offsets of one simulation.
-KParams lbpf_rt::make_kparams(const lbpf_params* p) {
+// Geometry, coefficients (FP64 and FP32) and link offsets of one simulation;
+// rows of sx >= nx elements (sx = 0: dense rows, sx = nx).
+KParams lbpf_rt::make_kparams(const lbpf_params* p, int sx) {
     KParams kp;
     kp.P = lattice_units(p);
+    if (sx > p->nx) {
+        kp.P.sx = sx;
+        kp.P.sxy = (long long)sx * p->ny;
+        kp.P.NS = kp.P.sxy * p->nz;
+    }
     kp.cd = make_coef<double>(kp.P);
     kp.cf = make_coef<float>(kp.P);
     const int q = p->lattice == LBPF_D3Q19 ? 19 : 9;
     const long long sb = p->precision == LBPF_FP64 ? 8 : (p->precision == LBPF_FP32 ? 4 : 2);
-    const bool fits = (long long)q * kp.P.N * sb < (1LL << 31);
+    const bool fits = (long long)q * kp.P.NS * sb < (1LL << 31);
     for (int k = 0; k < 19; ++k) {
         int e[3] = {0, 0, 0};
         if (k < q) {
             if (p->lattice == LBPF_D3Q19) { e[0] = D3Q19::ex(k); e[1] = D3Q19::ey(k); e[2] = D3Q19::ez(k); }
             else { e[0] = D2Q9::ex(k); e[1] = D2Q9::ey(k); }
         }
-        const long long nx = p->nx, nxy = (long long)p->nx * p->ny;
-        kp.kNB[k] = (long long)k * kp.P.N * sb;
+        const long long nx = kp.P.sx, nxy = kp.P.sxy;
+        kp.kNB[k] = (long long)k * kp.P.NS * sb;
         kp.koffB[k] = kp.kNB[k] - (e[0] + e[1] * nx + e[2] * nxy) * sb;
         kp.kNB32[k] = fits ? (int)kp.kNB[k] : 0;
         kp.koffB32[k] = fits ? (int)kp.koffB[k] : 0;
@@ -368,6 +377,7 @@ KParams lbpf_rt::march_kparams(const KParams& kp, int lattice) {
     if (lattice == LBPF_D2Q9) {
         m.P.nz = kp.P.ny;
         m.P.ny = 1;
+        m.P.sxy = kp.P.sx;      // a row is a plane of the march
         m.P.bc[2] = kp.P.bc[1];
         m.P.bc[1] = LBPF_PERIODIC;
     }

@@ -45,6 +45,11 @@ struct StepParams {
     int nx, ny, nz;
     int bc[3];          // 0 periodic, 1 bounce-back
     long long N;        // nx * ny * nz
+    // storage: node (x, y, z) at element z sxy + y sx + x of a field and of each
+    // population plane, population k starting at element k NS.  Single domains
+    // are dense (sx = nx, sxy = nx ny, NS = N); batch instances pad their rows.
+    int sx;
+    long long sxy, NS;
     double omg, omh;    // 1 / (tau + 1/2)
     double M;           // M_phi = tau_g / 3
     double gamma;       // 3 / tau_h
@@ -223,6 +228,15 @@ __device__ __forceinline__ int map_coord(int i, int n, int bc) {
     return i;
 }
 
+// Storage element of the node with dense index i = (z ny + y) nx + x.
+__host__ __device__ __forceinline__ long long storage_index(const StepParams& P, long long i) {
+    if (P.sx == P.nx) return i;     // dense: single domains (and unpadded instances)
+    const long long row = i / P.nx;
+    const long long x = i - row * P.nx;
+    const long long z = row / P.ny;
+    return z * P.sxy + (row - z * P.ny) * P.sx + x;
+}
+
 // e_k . v with the zero components dropped at compile time (k is a constant
 // after unrolling).
 template <class L, typename R>
@@ -362,7 +376,7 @@ struct HaloOffsets {
                 gx = map_coord(gx, P.nx, P.bc[0]);
                 gy = map_coord(gy, P.ny, P.bc[1]);
             }
-            o2[it] = s < G::P2 ? gy * P.nx + gx : 0;
+            o2[it] = s < G::P2 ? gy * P.sx + gx : 0;
         }
 #pragma unroll
         for (int it = 0; it < IT1; ++it) {
@@ -373,7 +387,7 @@ struct HaloOffsets {
                 gx = wrap1(gx, P.nx, P.bc[0]);
                 gy = wrap1(gy, P.ny, P.bc[1]);
             }
-            o1[it] = s < G::P1 ? gy * P.nx + gx : 0;
+            o1[it] = s < G::P1 ? gy * P.sx + gx : 0;
             c2[it] = (ly + G::OY2 - G::OY1) * G::X2 + (lx + 1);
         }
     }
@@ -386,7 +400,7 @@ __device__ __forceinline__ void async_phi_plane(const StepParams& P, const R* __
                                                 const HaloOffsets<G>& H) {
     const int tid = G::tid();
     const int gz = (L::D == 3) ? map_coord(zg, P.nz, P.bc[2]) : 0;
-    const R* src = phi + (long long)gz * P.nx * P.ny;
+    const R* src = phi + (long long)gz * P.sxy;
 #pragma unroll
     for (int it = 0; it < HaloOffsets<G>::IT2; ++it)
         if (tid + it * G::NT < G::P2) cp_async(dst + tid + it * G::NT, src + H.o2[it]);
@@ -398,7 +412,7 @@ __device__ __forceinline__ void async_ring(const StepParams& P, const R* __restr
                                            const HaloOffsets<G>& H) {
     const int tid = G::tid();
     const int gz = (L::D == 3) ? map_coord(zg, P.nz, P.bc[2]) : 0;
-    const R* src = f + (long long)gz * P.nx * P.ny;
+    const R* src = f + (long long)gz * P.sxy;
 #pragma unroll
     for (int it = 0; it < HaloOffsets<G>::IT1; ++it)
         if (tid + it * G::NT < G::P1) cp_async(dst + tid + it * G::NT, src + H.o1[it]);
@@ -527,8 +541,8 @@ __device__ __forceinline__ void pull_load(const KParams& K, const typename SP::s
                                           PullState<L, SP, IS_PHI, WALLS, I>& st) {
     using R = typename SP::real;
     const StepParams& P = K.P;
-    const I nxy = (I)P.nx * P.ny;
-    const I xi = (I)z * nxy + (I)y * P.nx + x;
+    const I nxy = (I)P.sxy;
+    const I xi = (I)z * nxy + (I)y * P.sx + x;
     st.xi = xi;
     st.wallmask = 0u;
     st.cx = IS_PHI ? R(0) : c_n[xi];
@@ -550,9 +564,9 @@ __device__ __forceinline__ void pull_load(const KParams& K, const typename SP::s
     }
     {
         const bool lo = y == 0, hi = y == P.ny - 1;
-        SY[1] = y * P.nx; WY[1] = false;
-        SY[2] = (lo ? (WALLS && P.bc[1] ? y : P.ny - 1) : y - 1) * P.nx; WY[2] = WALLS && lo && P.bc[1];
-        SY[0] = (hi ? (WALLS && P.bc[1] ? y : 0) : y + 1) * P.nx;        WY[0] = WALLS && hi && P.bc[1];
+        SY[1] = y * P.sx; WY[1] = false;
+        SY[2] = (lo ? (WALLS && P.bc[1] ? y : P.ny - 1) : y - 1) * P.sx; WY[2] = WALLS && lo && P.bc[1];
+        SY[0] = (hi ? (WALLS && P.bc[1] ? y : 0) : y + 1) * P.sx;        WY[0] = WALLS && hi && P.bc[1];
     }
     if (L::D == 3) {
         const bool lo = z == 0, hi = z == P.nz - 1;
@@ -841,16 +855,17 @@ __global__ void k_init(const KParams K, const typename SP::real* __restrict__ ph
     using R = typename SP::real;
     const StepParams& P = K.P;
     const Coef<R>& C = coef<R>(K);
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= P.N) return;
-    const int x = (int)(i % P.nx);
-    const int y = (int)((i / P.nx) % P.ny);
-    const int z = (int)(i / ((long long)P.nx * P.ny));
+    const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (id >= P.N) return;
+    const int x = (int)(id % P.nx);
+    const int y = (int)((id / P.nx) % P.ny);
+    const int z = (int)(id / ((long long)P.nx * P.ny));
+    const long long i = (long long)z * P.sxy + (long long)y * P.sx + x;     // storage element
     auto at = [&](int dx, int dy, int dz) {
         const int gx = map_coord(x + dx, P.nx, P.bc[0]);
         const int gy = map_coord(y + dy, P.ny, P.bc[1]);
         const int gz = (L::D == 3) ? map_coord(z + dz, P.nz, P.bc[2]) : 0;
-        return phi[((long long)gz * P.ny + gy) * P.nx + gx];
+        return phi[(long long)gz * P.sxy + (long long)gy * P.sx + gx];
     };
     R gx = 0, gy = 0, gz = 0;
 #pragma unroll
@@ -872,7 +887,7 @@ __global__ void k_init(const KParams K, const typename SP::real* __restrict__ ph
     for (int k = 0; k < L::Q; ++k) {
         const R wk = R(L::w(k));
         const R Gk = wk * (A + kct * edot<L>(k, gx, gy, gz));
-        SP::store(g, (long long)k * P.N + i, wk * ph - R(0.5) * Gk, wk * ph);
+        SP::store(g, (long long)k * P.NS + i, wk * ph - R(0.5) * Gk, wk * ph);
     }
     R hsum = R(0), hcomp = R(0);
 #pragma unroll
@@ -882,7 +897,7 @@ __global__ void k_init(const KParams K, const typename SP::real* __restrict__ ph
         const R heq = (k == 0) ? cc - R(LH::DEN - LH::m(0)) * Ps : R(LH::m(k)) * Ps;
         // H_k = gamma w_k e_k.F, or the flux part w_k e_k.F / xi_s^2 of h^eq,alt
         const R hk = P.h_eq_alt ? heq + R(3) * wk * f * ek : heq - R(0.5) * (C.gamma * wk * f * ek);
-        SP::store(h, (long long)k * P.N + i, hk, heq);
+        SP::store(h, (long long)k * P.NS + i, hk, heq);
         const R t = hsum + hk;              // Fast2Sum: h_0 (the largest) comes first
         hcomp += (hsum - t) + hk;
         hsum = t;
@@ -900,13 +915,23 @@ __global__ void k_from_f64(const double* __restrict__ src, R* __restrict__ dst, 
     if (i < n) dst[i] = R(src[i]);
 }
 
+// Dense FP64 caller data (rows of nx) -> rows of pitch sx in the compute type.
+template <typename R>
+__global__ void k_from_f64_rows(const double* __restrict__ src, R* __restrict__ dst, long long n, int nx, int sx) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const long long row = i / nx;
+    dst[row * sx + (i - row * nx)] = R(src[i]);
+}
+
 template <typename R>
 __global__ void k_fields_out(const KParams K, const R* __restrict__ phi, const R* __restrict__ c,
                              double* __restrict__ ophi, double* __restrict__ oc, double* __restrict__ omu) {
     const StepParams& P = K.P;
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= P.N) return;
-    const double ph = (double)phi[i], cc = (double)c[i];
+    const long long j = storage_index(P, i);
+    const double ph = (double)phi[j], cc = (double)c[j];
     if (ophi) ophi[i] = ph;
     if (oc) oc[i] = cc;
     if (omu)
@@ -925,17 +950,18 @@ __global__ void k_pops_out(const KParams K, const typename SP::real* __restrict_
     const Coef<R>& C = coef<R>(K);
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= P.N) return;
-    const R ph = phi[i], cc = c[i];
+    const long long j = storage_index(P, i);
+    const R ph = phi[j], cc = c[j];
     const R Ps = divw<LH::DEN>(p_term(C, ph, closure_mu(C, ph, cc)));
 #pragma unroll
     for (int k = 0; k < L::Q; ++k) {
         const R wk = R(L::w(k));
-        if (og) og[(long long)k * P.N + i] = (double)SP::load(g, (long long)k * P.N + i, wk * ph);
+        if (og) og[(long long)k * P.N + i] = (double)SP::load(g, (long long)k * P.NS + j, wk * ph);
     }
 #pragma unroll
     for (int k = 0; k < LH::Q; ++k) {
         const R heq = (k == 0) ? cc - R(LH::DEN - LH::m(0)) * Ps : R(LH::m(k)) * Ps;
-        if (oh) oh[(long long)k * P.N + i] = (double)SP::load(h, (long long)k * P.N + i, heq);
+        if (oh) oh[(long long)k * P.N + i] = (double)SP::load(h, (long long)k * P.NS + j, heq);
     }
 }
 
@@ -1083,14 +1109,15 @@ k_pop_mass(const KParams K, const typename SP::real* __restrict__ phi, const typ
     const StepParams& P = K.P;
     const Coef<R>& C = coef<R>(K);
     MassAcc<R> acc{R(0), R(0)};
-    for (long long i = blockIdx.x * (long long)kMassThreads + threadIdx.x; i < P.N;
-         i += (long long)gridDim.x * kMassThreads) {
+    for (long long id = blockIdx.x * (long long)kMassThreads + threadIdx.x; id < P.N;
+         id += (long long)gridDim.x * kMassThreads) {
+        const long long i = storage_index(P, id);
         const R ph = phi[i], cc = c[i];
         const R Ps = divw<L::DEN>(p_term(C, ph, closure_mu(C, ph, cc)));
 #pragma unroll
         for (int k = 0; k < L::Q; ++k) {
             const R ref = (k == 0) ? cc - R(L::DEN - L::m(0)) * Ps : R(L::m(k)) * Ps;
-            acc.add(SP::load(h, (long long)k * P.N + i, ref), R(0));
+            acc.add(SP::load(h, (long long)k * P.NS + i, ref), R(0));
         }
     }
     double v = (double)acc.hi + (double)acc.lo, d1 = 0.0, d2 = 0.0;
