@@ -40,6 +40,12 @@ dim3 adj_grid(const lbpf_ctx* ctx) {
     return dim3((P.nx + kAdjBX - 1) / kAdjBX, (P.ny + kAdjBY - 1) / kAdjBY, std::min(P.nz, 32768));
 }
 
+}  // namespace
+
+int adjoint_max_ny() { return kAdjBY * 65535; }
+
+namespace {
+
 int adj_blocks(const lbpf_ctx* ctx) {
     const dim3 g = adj_grid(ctx);
     return (int)(g.x * g.y * g.z);

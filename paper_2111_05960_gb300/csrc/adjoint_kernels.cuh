@@ -45,10 +45,17 @@ struct AdjWork {        // per-node partial adjoints, SoA, N entries each
     R* grad;            // grad phi, [3][N]
 };
 
-constexpr int kAdjBX = 32, kAdjBY = 8, kAdjThreads = kAdjBX * kAdjBY;
-// resident blocks per SM the link kernels are compiled for (register budget)
+#ifndef LBPF_ADJ_BY
+#define LBPF_ADJ_BY 8
+#endif
+constexpr int kAdjBX = 32, kAdjBY = LBPF_ADJ_BY, kAdjThreads = kAdjBX * kAdjBY;
+// resident blocks per SM the link kernels are compiled for (register budget).
+// FP32 on GB300, reverse sweep of the 128^3 differentiable workload: 4 blocks
+// (64 registers, 300-390 bytes of spills) 0.36 ms per step, 3 blocks (80
+// registers, 136 / 12 bytes spilled by the h / g kernel) 0.32 ms, 2 blocks (128
+// registers, none spilled) 0.35 ms.
 #ifndef LBPF_ADJ_MINB_F32
-#define LBPF_ADJ_MINB_F32 4
+#define LBPF_ADJ_MINB_F32 3
 #endif
 #ifndef LBPF_ADJ_MINB_F64
 #define LBPF_ADJ_MINB_F64 2

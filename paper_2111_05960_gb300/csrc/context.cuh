@@ -140,6 +140,7 @@ void launch_from_f64_rows(const double* src, void* dst, long long n, int nx, int
 
 // adjoint.cu
 const AdjDispatch* pick_adjoint(int lattice, int precision);
+int adjoint_max_ny();   // rows its kernels' grid covers (tile rows x 65535 blocks)
 size_t state_bytes_for(const lbpf_ctx* ctx);
 StateView state_view(const lbpf_ctx* ctx, void* base);
 lbpf_status record_checkpoint(lbpf_ctx* ctx);   // the current state, when step % k == 0

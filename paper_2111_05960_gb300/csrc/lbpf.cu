@@ -558,7 +558,9 @@ lbpf_status lbpf_create(const lbpf_params* p, const double* phi0, const double* 
                         "the adjoint covers h on the lattice of g with H_k and equal curvatures only");
         aops = pick_adjoint(p->lattice, p->precision);
         if (!aops) return fail(nullptr, LBPF_EUNSUPPORTED, "the adjoint is built for FP64 and FP32 storage only");
-        if (p->ny > 8 * 65535) return fail(nullptr, LBPF_EUNSUPPORTED, "the adjoint needs ny <= 524280");
+        if (p->ny > adjoint_max_ny())
+            return fail(nullptr, LBPF_EUNSUPPORTED,
+                        "the adjoint needs ny <= " + std::to_string(adjoint_max_ny()) + " (its grid's y extent)");
     }
 
     lbpf_ctx* ctx = new (std::nothrow) lbpf_ctx();
