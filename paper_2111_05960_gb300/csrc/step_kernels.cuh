@@ -995,17 +995,84 @@ __device__ __forceinline__ void block_sum3(double& a, double& b, double& c) {
     }
 }
 
+// Field sums for lbpf_mass: Sum c, Sum phi and the count of nodes outside the
+// stable range, per block.  The fields are the context's own dense arrays
+// (16-byte aligned); each thread keeps 2 x UNR vector loads per array in
+// flight, so that the pass runs at the speed of its memory traffic instead of
+// one load latency per element.
 template <typename R>
 __global__ void __launch_bounds__(kMassThreads)
 k_mass_partial(const R* __restrict__ c, const R* __restrict__ phi, long long n, double* __restrict__ partials) {
+    constexpr int UNR = 4;
     double sc = 0.0, sp = 0.0, bad = 0.0;
-    for (long long i = blockIdx.x * (long long)kMassThreads + threadIdx.x; i < n;
-         i += (long long)gridDim.x * kMassThreads) {
-        const double cv = (double)c[i], pv = (double)phi[i];
-        sc += cv;
-        sp += pv;
-        // non-finite values fail both comparisons and count as bad
-        if (!(pv >= -0.5 && pv <= 1.5) || !(cv == cv && cv - cv == 0.0)) bad += 1.0;
+    const long long stride = (long long)gridDim.x * kMassThreads * UNR;
+    if constexpr (sizeof(R) == 4) {
+        // FP32 fields: exact float-float partial sums (TwoSum) of each thread's
+        // 16 values per round, then added in FP64, and the range tests in FP32
+        // (the FP64 pipe runs at a small fraction of the FP32 rate).
+        const long long n4 = n / 4;
+        const float4* c4 = reinterpret_cast<const float4*>(c);
+        const float4* p4 = reinterpret_cast<const float4*>(phi);
+        unsigned nbad = 0;
+        auto take = [&](float cv, float pv, MassAcc<float>& ac, MassAcc<float>& ap) {
+            ac.add(cv, 0.0f);
+            ap.add(pv, 0.0f);
+            // non-finite values fail both comparisons and count as bad
+            if (!(pv >= -0.5f && pv <= 1.5f) || !(cv == cv && cv - cv == 0.0f)) ++nbad;
+        };
+        for (long long j0 = (long long)blockIdx.x * kMassThreads * UNR + threadIdx.x; j0 < n4; j0 += stride) {
+            float4 cv[UNR], pv[UNR];
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                const long long j = j0 + (long long)u * kMassThreads;
+                cv[u] = j < n4 ? c4[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+                pv[u] = j < n4 ? p4[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            MassAcc<float> ac{0.0f, 0.0f}, ap{0.0f, 0.0f};
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                take(cv[u].x, pv[u].x, ac, ap);
+                take(cv[u].y, pv[u].y, ac, ap);
+                take(cv[u].z, pv[u].z, ac, ap);
+                take(cv[u].w, pv[u].w, ac, ap);
+            }
+            sc += (double)ac.hi + (double)ac.lo;
+            sp += (double)ap.hi + (double)ap.lo;
+        }
+        if (blockIdx.x == 0) {               // the last n mod 4 values
+            for (long long i = 4 * n4 + threadIdx.x; i < n; i += kMassThreads) {
+                MassAcc<float> ac{0.0f, 0.0f}, ap{0.0f, 0.0f};
+                take(c[i], phi[i], ac, ap);
+                sc += (double)ac.hi;
+                sp += (double)ap.hi;
+            }
+        }
+        bad = (double)nbad;
+    } else {
+        const long long n2 = n / 2;
+        const double2* c2 = reinterpret_cast<const double2*>(c);
+        const double2* p2 = reinterpret_cast<const double2*>(phi);
+        auto take = [&](double cv, double pv) {
+            sc += cv;
+            sp += pv;
+            if (!(pv >= -0.5 && pv <= 1.5) || !(cv == cv && cv - cv == 0.0)) bad += 1.0;
+        };
+        for (long long j0 = (long long)blockIdx.x * kMassThreads * UNR + threadIdx.x; j0 < n2; j0 += stride) {
+            double2 cv[UNR], pv[UNR];
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                const long long j = j0 + (long long)u * kMassThreads;
+                cv[u] = j < n2 ? c2[j] : make_double2(0.0, 0.0);
+                pv[u] = j < n2 ? p2[j] : make_double2(0.0, 0.0);
+            }
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                take(cv[u].x, pv[u].x);
+                take(cv[u].y, pv[u].y);
+            }
+        }
+        if (blockIdx.x == 0)
+            for (long long i = 2 * n2 + threadIdx.x; i < n; i += kMassThreads) take(c[i], phi[i]);
     }
     block_sum3<R>(sc, sp, bad);
     if (threadIdx.x == 0) {
@@ -1056,6 +1123,9 @@ static __global__ void __launch_bounds__(kMassThreads)
 k_mass_corr_plan(const double* __restrict__ partials, int nblocks, MassCorr* __restrict__ mc, long long N,
                  double delta_target) {
     double sc = 0.0, d1 = 0.0, d2 = 0.0;
+    // unrolled so that a thread's loads are in flight together (the adds keep
+    // their order, so the sum does not depend on the unrolling)
+#pragma unroll 16
     for (int b = threadIdx.x; b < nblocks; b += kMassThreads) sc += partials[b];
     block_sum3<double>(sc, d1, d2);
     if (threadIdx.x == 0) {
