@@ -208,6 +208,17 @@ lbpf_status lbpf_get_populations(lbpf_ctx *ctx, double *g, double *h, int32_t pt
  * Synchronises. */
 lbpf_status lbpf_step_timed(lbpf_ctx *ctx, int64_t nsteps, double *kernel_ms);
 
+/* How the context's step kernels read the populations they pull:
+ * *tensor_maps = 1 when the copy engine brings each plane's population rows
+ * into shared memory through tensor maps of the context's buffers, 0 when
+ * every thread loads its own.  The tensor-map form is opt-in: the environment
+ * variable LBPF_TMA=1 at creation, FP32 storage on D3Q19, every axis periodic,
+ * nx a multiple of 4 and at least 40.  Its results are bit-identical to the
+ * load form; it is about twice slower on GB300 (one copy request per link,
+ * tile and plane), so it is not the default.  Needs no GPU work.
+ * Errors: EINVAL (ctx or tensor_maps NULL). */
+lbpf_status lbpf_pull_path(const lbpf_ctx *ctx, int32_t *tensor_maps);
+
 /* Measured FP64 FMA throughput of the current device in TFLOP/s (*tflops),
  * from a kernel of independent FMA chains on every SM (about a second of
  * work at 1 TFLOP/s scale), timed with CUDA events on cuda_stream (NULL =

@@ -30,6 +30,7 @@ struct Dispatch {
     void (*launch_c_p)(lbpf_ctx*, const void* h, void* h_out, const void* phi, const void* phi_out, const void* c,
                        void* c_out, double* mass_partials);
     void (*launch_corr_p)(lbpf_ctx*, lbpf::MassCorr* mc, void* c, void* h);
+    bool (*setup_tensor_maps)(lbpf_ctx*);   // true: the step kernels pull through tensor maps
 };
 // Launchers of a batch of 2-D instances; the step kernels use the tile shape
 // ctx->btile (an index into lbpf::kBatchTiles), which prepare() sets up.
@@ -71,7 +72,12 @@ struct lbpf_ctx {
     void* c[2] = {nullptr, nullptr};
     double* staging = nullptr;     // 3 N doubles, allocated on first host transfer
     double* partials = nullptr;    // mass reduction scratch
-    double* mass_out = nullptr;    // 3 doubles
+    double* mass_out = nullptr;    // 3 doubles, then the device error flag (see d_err)
+    int* d_err = nullptr;          // set by a kernel whose bounded wait ran out (inside mass_out[3])
+    // tensor maps of the population buffers (pulls by the copy engine) and an
+    // unused one for the kernels that pull with loads
+    bool tma = false;
+    CUtensorMap gmap[2], hmap[2], nomap;
     double* corr_partials = nullptr;   // one FP64 mass per composition-kernel block
     lbpf::MassCorr* corr = nullptr;    // closed-loop mass correction state (device)
     int corr_blocks = 0;

@@ -118,6 +118,9 @@ namespace {
 #ifndef LBPF_MINB3_HS
 #define LBPF_MINB3_HS 4
 #endif
+#ifndef LBPF_MINB3_TMA
+#define LBPF_MINB3_TMA 5
+#endif
 // Increment per corrected node of the mass correction: ~100 ulps of an FP32
 // value near 1, so that each node's rounding is ~1% of the increment.
 constexpr double kCorrDelta = 1e-5;
@@ -148,6 +151,35 @@ struct TileCfg<D3Q19, true> {
     static constexpr int BX = 32, BY = LBPF_BY3_F64, ZCH = LBPF_ZCH3_F64, MINB = LBPF_MINB3_F64;
 };
 
+// Tensor map of one population buffer as a 4-D array (x, y, z, k) with the
+// row, plane and population strides of P, read in boxes of box_x x box_y x 1 x 1
+// values; rows and columns outside the grid read as zeros.
+using TensorMapEncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                          const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                                          CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                          CUtensorMapFloatOOBfill);
+bool encode_pop_map(CUtensorMap* m, void* base, const StepParams& P, int q, int box_x, int box_y) {
+    static const TensorMapEncodeTiled encode = []() -> TensorMapEncodeTiled {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult qr = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &qr) !=
+                cudaSuccess ||
+            qr != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return reinterpret_cast<TensorMapEncodeTiled>(f);
+    }();
+    if (!encode) return false;
+    const cuuint64_t dims[4] = {(cuuint64_t)P.nx, (cuuint64_t)P.ny, (cuuint64_t)P.nz, (cuuint64_t)q};
+    const cuuint64_t strides[3] = {(cuuint64_t)P.sx * 4, (cuuint64_t)P.sxy * 4, (cuuint64_t)P.NS * 4};
+    const cuuint32_t box[4] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1, 1};
+    const cuuint32_t elem[4] = {1, 1, 1, 1};
+    return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, elem, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // HS: h on the small lattice of L (D2Q5 / D3Q7) instead of L itself.
 template <class L, class SP, bool HS = false>
 struct Impl {
@@ -162,10 +194,20 @@ struct Impl {
     static constexpr int BYC = TC::BY, ZCHC = TC::ZCH, MINBC = TC::MINB;
     static constexpr size_t smem_phi = march_smem<ML, SP, BY, BX>(true);
     static constexpr size_t smem_c = march_smem<ML, SP, BYC, BX>(false);
-    template <bool W>
-    static constexpr auto kphi() { return k_phi_step<ML, SP, BY, MINB, W, BX>; }
-    template <bool W>
-    static constexpr auto kc() { return k_c_step<ML, SP, BYC, MINBC, W, BX, MLH>; }
+    // pulls through tensor maps: FP32 storage on the 3-D lattices, periodic
+    // domains (the kernels' TMA form)
+    static constexpr bool TMA_OK = std::is_same<S, float>::value && L::D == 3;
+    static constexpr size_t smem_phi_t = march_smem<ML, SP, BY, BX, MLH>(true, true);
+    static constexpr size_t smem_c_t = march_smem<ML, SP, BYC, BX, MLH>(false, true);
+    static_assert(smem_phi_t <= 227 * 1024 && smem_c_t <= 227 * 1024, "a block's shared memory");
+    // the TMA kernels' stages take ~24 KB more shared memory per block: 5
+    // resident blocks, so they are compiled for 5
+    template <bool W, bool T = false>
+    static constexpr auto kphi() { return k_phi_step<ML, SP, BY, T ? LBPF_MINB3_TMA : MINB, W, BX, T>; }
+    template <bool W, bool T = false>
+    static constexpr auto kc() {
+        return k_c_step<ML, SP, BYC, T ? (LBPF_MINB3_TMA < MINBC ? LBPF_MINB3_TMA : MINBC) : MINBC, W, BX, MLH, T>;
+    }
 
     static lbpf_status prepare(lbpf_ctx* ctx) {
         ctx->zch_phi = ZCH;
@@ -174,7 +216,29 @@ struct Impl {
         LBPF_CUDA(ctx, cudaFuncSetAttribute(kc<true>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
         LBPF_CUDA(ctx, cudaFuncSetAttribute(kphi<false>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_phi));
         LBPF_CUDA(ctx, cudaFuncSetAttribute(kc<false>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
+        if constexpr (TMA_OK) {
+            LBPF_CUDA(ctx, cudaFuncSetAttribute(kphi<false, true>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)smem_phi_t));
+            LBPF_CUDA(ctx, cudaFuncSetAttribute(kc<false, true>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)smem_c_t));
+        }
         return LBPF_OK;
+    }
+    // maps of the context's g and h buffers for the TMA kernels; false: this
+    // context pulls with loads (walls, 16-bit or FP64 storage, rows whose byte
+    // stride is not a multiple of 16, or a grid narrower than one box)
+    static bool setup_tensor_maps(lbpf_ctx* ctx) {
+        if constexpr (!TMA_OK) {
+            return false;
+        } else {
+            const StepParams& P = ctx->kpm.P;
+            if (walls(ctx) || P.sx != P.nx || P.nx % 4 != 0 || P.nx < BX + 8) return false;
+            for (int i = 0; i < 2; ++i) {
+                if (!encode_pop_map(&ctx->gmap[i], ctx->g[i], P, ML::Q, BX + 8, BY)) return false;
+                if (!encode_pop_map(&ctx->hmap[i], ctx->h[i], P, MLH::Q, BX + 8, BYC)) return false;
+            }
+            return true;
+        }
     }
     static bool walls(const lbpf_ctx* ctx) {
         const StepParams& P = ctx->sp;
@@ -193,21 +257,39 @@ struct Impl {
                              void* phi_out) {
         auto kern = walls(ctx) ? kphi<true>() : kphi<false>();
         kern<<<grid(ctx), dim3(BX, BY), smem_phi, ctx->stream>>>(ctx->kpm, (const S*)g, (S*)g_out, (const R*)phi,
-                                                                   (const R*)c, (R*)phi_out, ctx->zch_phi);
+                                                                   (const R*)c, (R*)phi_out, ctx->zch_phi,
+                                                                   ctx->nomap, ctx->d_err);
     }
     static void launch_c_p(lbpf_ctx* ctx, const void* h, void* h_out, const void* phi, const void* phi_out,
                            const void* c, void* c_out, double* mass_partials) {
         auto kern = walls(ctx) ? kc<true>() : kc<false>();
         kern<<<grid_c(ctx), dim3(BX, BYC), smem_c, ctx->stream>>>(ctx->kpm, (const S*)h, (S*)h_out, (const R*)phi,
                                                                  (const R*)phi_out, (const R*)c, (R*)c_out,
-                                                                 mass_partials, ctx->zch_c);
+                                                                 mass_partials, ctx->zch_c, ctx->nomap, ctx->d_err);
     }
     static void launch_phi(lbpf_ctx* ctx, int cur) {
         const int nxt = cur ^ 1;
+        if constexpr (TMA_OK) {
+            if (ctx->tma) {
+                kphi<false, true>()<<<grid(ctx), dim3(BX, BY), smem_phi_t, ctx->stream>>>(
+                    ctx->kpm, (const S*)ctx->g[cur], (S*)ctx->g[nxt], (const R*)ctx->phi[cur], (const R*)ctx->c[cur],
+                    (R*)ctx->phi[nxt], ctx->zch_phi, ctx->gmap[cur], ctx->d_err);
+                return;
+            }
+        }
         launch_phi_p(ctx, ctx->g[cur], ctx->g[nxt], ctx->phi[cur], ctx->c[cur], ctx->phi[nxt]);
     }
     static void launch_c(lbpf_ctx* ctx, int cur, double* mass_partials) {
         const int nxt = cur ^ 1;
+        if constexpr (TMA_OK) {
+            if (ctx->tma) {
+                kc<false, true>()<<<grid_c(ctx), dim3(BX, BYC), smem_c_t, ctx->stream>>>(
+                    ctx->kpm, (const S*)ctx->h[cur], (S*)ctx->h[nxt], (const R*)ctx->phi[cur],
+                    (const R*)ctx->phi[nxt], (const R*)ctx->c[cur], (R*)ctx->c[nxt], mass_partials, ctx->zch_c,
+                    ctx->hmap[cur], ctx->d_err);
+                return;
+            }
+        }
         launch_c_p(ctx, ctx->h[cur], ctx->h[nxt], ctx->phi[cur], ctx->phi[nxt], ctx->c[cur], ctx->c[nxt],
                    mass_partials);
     }
@@ -246,7 +328,7 @@ struct Impl {
     static const Dispatch* table() {
         static const Dispatch d = {prepare,         launch_phi,   launch_c,   launch_init,
                                    launch_pops_out, launch_corr,  launch_pop_mass, c_blocks,
-                                   launch_phi_p,    launch_c_p,   launch_corr_p};
+                                   launch_phi_p,    launch_c_p,   launch_corr_p, setup_tensor_maps};
         return &d;
     }
 };
@@ -600,8 +682,19 @@ lbpf_status lbpf_create(const lbpf_params* p, const double* phi0, const double* 
     ctx->mass_blocks = (int)std::min<long long>(want, 4LL * sms);
     if (ctx->mass_blocks < 1) ctx->mass_blocks = 1;
     if ((st = alloc(ctx, (void**)&ctx->partials, sizeof(double) * 3 * ctx->mass_blocks, "mass partials")) != LBPF_OK) return abort_create(st);
-    if ((st = alloc(ctx, (void**)&ctx->mass_out, sizeof(double) * 3, "mass result")) != LBPF_OK) return abort_create(st);
+    if ((st = alloc(ctx, (void**)&ctx->mass_out, sizeof(double) * 4, "mass result")) != LBPF_OK) return abort_create(st);
+    ctx->d_err = reinterpret_cast<int*>(ctx->mass_out + 3);
+    e = cudaMemsetAsync(ctx->mass_out, 0, sizeof(double) * 4, ctx->stream);
+    if (e != cudaSuccess) { cuda_fail(ctx, e, "mass result"); return abort_create(LBPF_ECUDA); }
     if ((st = ops->prepare(ctx)) != LBPF_OK) return abort_create(st);
+    std::memset(&ctx->nomap, 0, sizeof(ctx->nomap));
+    {
+        // the tensor-map pulls are opt-in (LBPF_TMA=1): bit-identical to the
+        // load path, but twice slower at 256^3 (one copy-engine request per
+        // link and plane: 19 boxes of 4 rows per 32 x 4 tile and plane)
+        const char* tma = getenv("LBPF_TMA");
+        ctx->tma = tma && strcmp(tma, "1") == 0 && ops->setup_tensor_maps(ctx);
+    }
 
     const double* sphi = phi0;
     const double* sc = c0;
@@ -651,6 +744,12 @@ lbpf_status lbpf_step(lbpf_ctx* ctx, int64_t nsteps) {
     if (ctx->poisoned) return fail(ctx, LBPF_ESTATE, "context poisoned by an earlier error");
     if (nsteps < 0) return fail(ctx, LBPF_EINVAL, "nsteps < 0");
     return run_steps(ctx, nsteps);
+}
+
+lbpf_status lbpf_pull_path(const lbpf_ctx* ctx, int32_t* tensor_maps) {
+    if (!ctx || !tensor_maps) return fail(nullptr, LBPF_EINVAL, "ctx or tensor_maps is NULL");
+    *tensor_maps = ctx->tma ? 1 : 0;
+    return LBPF_OK;
 }
 
 lbpf_status lbpf_step_timed(lbpf_ctx* ctx, int64_t nsteps, double* kernel_ms) {
@@ -712,9 +811,15 @@ lbpf_status lbpf_mass(lbpf_ctx* ctx, double* total_c, double* total_phi) {
     if (is_f64(ctx)) launch_mass<double>(ctx); else launch_mass<float>(ctx);
     lbpf_status st = check_launch(ctx, "mass kernels");
     if (st != LBPF_OK) return st;
-    double hostv[3];
+    double hostv[4];
     LBPF_CUDA(ctx, cudaMemcpyAsync(hostv, ctx->mass_out, sizeof(hostv), cudaMemcpyDeviceToHost, ctx->stream));
     LBPF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    int dev_err = 0;
+    std::memcpy(&dev_err, &hostv[3], sizeof(int));
+    if (dev_err != 0) {
+        ctx->poisoned = true;
+        return fail(ctx, LBPF_ECUDA, "a tensor copy of the step kernels did not complete (bounded wait ran out)");
+    }
     if (total_c) *total_c = hostv[0];
     if (total_phi) *total_phi = hostv[1];
     if (hostv[2] != 0.0 || !std::isfinite(hostv[0]) || !std::isfinite(hostv[1])) {

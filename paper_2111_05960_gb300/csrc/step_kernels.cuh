@@ -30,6 +30,7 @@
 // stencil sees mirror ghosts phi(-1) = phi(0), phi(-2) = phi(1).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -353,6 +354,49 @@ __device__ __forceinline__ void cp_async(R* smem_dst, const R* gsrc) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Tensor-memory-access (TMA) copies of population rows, completed on an
+// mbarrier in shared memory.  One thread arms the barrier with the byte count
+// of a plane and issues the tiled copies; every thread waits on the barrier's
+// phase before it reads the rows.
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+// orders this thread's shared-memory accesses before later copy-engine accesses
+// (after barrier initialisation, and after writes into a stage the engine refills)
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// Bounded wait: each try suspends for a hardware-chosen time, and 2^20 tries
+// end well within a second.  false: the phase never completed.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+    for (int i = 0; i < (1 << 20); ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+// Box of a 4-D tensor map at coordinates (c0 innermost .. c3) into shared memory.
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];\n" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
+        : "memory");
+}
+
 // In-plane offsets (y nx + x, wrapped on periodic axes, mirrored at walls) of
 // the window elements this thread copies: the phi plane with its 2-node halo
 // (o2) and the 1-node ring (o1), and the phi-window index of each ring node it
@@ -533,6 +577,7 @@ struct PullState {
     R cx;
     unsigned wallmask;
     I xi;
+    const R* srow;   // tensor-map pulls: this thread's column of the stage (see tma_pull)
 };
 
 template <class L, class SP, bool IS_PHI, bool WALLS, typename I>
@@ -588,10 +633,60 @@ __device__ __forceinline__ void pull_load(const KParams& K, const typename SP::s
     }
 }
 
+// The slots of the links whose upstream node lies across an x or y face:
+// the wrapped node's value.  Out of line, so that the registers it needs do
+// not weigh on the march (only threads on those faces call it).
+template <class L, int BOXE, typename R>
+__device__ __noinline__ void tma_fix_edges(const R* __restrict__ fin, int nx, int ny, int nz, long long sx,
+                                           long long sxy, long long ns, int x, int y, int z, R* row) {
+#pragma unroll 1
+    for (int k = 0; k < L::Q; ++k) {
+        const int ex = L::ex(k), ey = L::ey(k);
+        const int ux = x - ex, uy = y - ey;
+        if (ux < 0 || ux >= nx || uy < 0 || uy >= ny) {
+            const int xs = ux < 0 ? ux + nx : (ux >= nx ? ux - nx : ux);
+            const int ys = uy < 0 ? uy + ny : (uy >= ny ? uy - ny : uy);
+            int zs = z - L::ez(k);
+            zs = zs < 0 ? zs + nz : (zs >= nz ? zs - nz : zs);
+            row[k * BOXE - ex] = fin[k * ns + zs * sxy + ys * sx + xs];
+        }
+    }
+}
+
+// Pull of plane z from the rows the copy engine placed in shared memory (the
+// tensor-map path: all axes periodic, FP32 storage).  Link k's box holds rows
+// y0 - ey .. y0 - ey + BY - 1 of plane z - ez (wrapped), columns x0 - 4 ..
+// x0 + BX + 3, so the thread at (tx, ty) finds its upstream value at row ty,
+// column tx + 4 - ex, a slot no other thread reads; the collision reads it
+// there.  A box row or column outside the grid was filled with zeros: the
+// threads on the grid's x or y faces (`edge`) overwrite those slots with the
+// wrapped node's value.  `fix`: some lane of the warp is such a thread.
+template <class L, class SP, int BX, int BY, bool IS_PHI, bool WALLS, typename I>
+__device__ __forceinline__ void tma_pull(const KParams& K, const typename SP::store_t* __restrict__ fin,
+                                         const typename SP::real* __restrict__ c_n, int x, int y, int z,
+                                         typename SP::real* stage, bool edge, bool fix,
+                                         PullState<L, SP, IS_PHI, WALLS, I>& st) {
+    using R = typename SP::real;
+    constexpr int TXW = BX + 8, BOXE = TXW * BY;
+    const StepParams& P = K.P;
+    const I xi = (I)z * (I)P.sxy + (I)y * P.sx + x;
+    st.xi = xi;
+    st.wallmask = 0u;
+    st.cx = IS_PHI ? R(0) : c_n[xi];
+    R* row = stage + threadIdx.y * TXW + threadIdx.x + 4;
+    st.srow = row;
+    if (fix) {
+        if (edge) tma_fix_edges<L, BOXE>(fin, P.nx, P.ny, P.nz, (long long)P.sx, (long long)P.sxy, (long long)P.NS,
+                                         x, y, z, row);
+        // these generic writes come before the copy engine refills the stage
+        fence_proxy_async();
+    }
+}
+
 // Collision of each pulled population at its upstream node from the ingredient
 // planes im (z-1), i0 (z), ip (z+1) (phi planes fm, f0, fp likewise), the new
 // moment, and the stores.
-template <class L, class SP, int BY, int BX, bool IS_PHI, bool WALLS, typename I, bool U>
+template <class L, class SP, int BY, int BX, bool IS_PHI, bool WALLS, typename I, bool U, bool TS = false>
 __device__ __forceinline__ void pull_combine(const KParams& K, const Coef<typename SP::real>& C,
                                              typename SP::store_t* __restrict__ fout,
                                              const V4<typename SP::real>* im, const V4<typename SP::real>* i0,
@@ -625,7 +720,8 @@ __device__ __forceinline__ void pull_combine(const KParams& K, const Coef<typena
     if (!IS_PHI) {
         // rest population of h: h*_0 = (1 - w_h) h_0 + w_h h^eq_0 (H_0 = 0)
         const R heq0 = st.cx - R(L::DEN - L::m(0)) * i0[c1].a;   // h^eq_0 = c - (1 - w_0) P
-        v[0] = keep * (SP::deviation ? st.old[0] + heq0 : st.old[0]) + om * heq0;
+        const R old0 = TS ? st.srow[0] : st.old[0];
+        v[0] = keep * (SP::deviation ? old0 + heq0 : old0) + om * heq0;
         sum = v[0];
         if (!hold) SP::store(byte_add(out, link_base<I>(K, 0)), 0, v[0], R(0));
     }
@@ -638,7 +734,7 @@ __device__ __forceinline__ void pull_combine(const KParams& K, const Coef<typena
         const R* fk = L::ez(k) > 0 ? fm : (L::ez(k) < 0 ? fp : f0);
         const V4<R> g = wall ? i0[c1] : ik[c1 - L::ex(k) - G::X1 * L::ey(k)];
         const R sgn = wall ? R(-1) : R(1);
-        R f_old = st.old[k];
+        R f_old = TS ? st.srow[k * (BX + 8) * BY - L::ex(k)] : st.old[k];
         if (SP::deviation) {
             const R ref = IS_PHI ? wk * (wall ? f0[c2] : fk[c2 - L::ex(k) - G::X2 * L::ey(k)]) : mk * g.a;
             f_old += ref;
@@ -710,21 +806,32 @@ __device__ __forceinline__ void block_mass_out(const MassAcc<R>& m, double* __re
 // One z-marching pass of either kernel over the planes z0 <= z < z1 of the tile
 // at (x0, y0).  The composition kernel also adds the exact mass of the
 // populations it writes to macc.
+// TMA: the pulls come from tensor-map copies (tmap: the 4-D map of fin, see
+// tma_pull); a copy that never lands sets *err after a bounded wait.
 template <class L, class SP, int BY, bool IS_PHI, bool WALLS, int BX = 32, typename I = long long,
-          class LH = L, bool U = true>
+          class LH = L, bool U = true, bool TMA = false>
 __device__ __forceinline__ void march(const KParams& K, const typename SP::store_t* __restrict__ fin,
                                       typename SP::store_t* __restrict__ fout,
                                       const typename SP::real* __restrict__ phi_n,
                                       const typename SP::real* __restrict__ phi_np1,
                                       const typename SP::real* __restrict__ c_n,
                                       typename SP::real* __restrict__ moment_out,
-                                      MassAcc<typename SP::real>& macc, int x0, int y0, int z0, int z1) {
+                                      MassAcc<typename SP::real>& macc, int x0, int y0, int z0, int z1,
+                                      const CUtensorMap* tmap = nullptr, int* err = nullptr) {
     using R = typename SP::real;
     using G = Geo<L, BY, BX>;
     const StepParams& P = K.P;
     const Coef<R>& C = coef<R>(K);
-    extern __shared__ __align__(32) unsigned char smem_raw[];
-    V4<R>* sing = reinterpret_cast<V4<R>*>(smem_raw);                 // [NING][P1]
+    static_assert(!TMA || (std::is_same<typename SP::store_t, float>::value && !WALLS && !L::FLAT_Y && BX == 32),
+                  "tensor-map pulls: FP32 storage, periodic 3-D tiles");
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // tensor-map stages first (128-byte aligned boxes), then their two barriers
+    constexpr int TXW = BX + 8, BOXE = TXW * BY;
+    constexpr int TSTAGE = TMA ? LH::Q * BOXE : 0;               // elements of one stage
+    R* tst = reinterpret_cast<R*>(smem_raw);                         // [2][LH::Q][BY][TXW]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(tst + 2 * TSTAGE);   // [2] (TMA only)
+    unsigned char* rest = smem_raw + (TMA ? 2 * TSTAGE * sizeof(R) + 16 : 0);
+    V4<R>* sing = reinterpret_cast<V4<R>*>(rest);                    // [NING][P1]
     R* sphi = reinterpret_cast<R*>(sing + G::NING * G::P1);          // [NPHI][P2]
     R* cst = sphi + G::NPHI * G::P2;                                 // [2][P1] c^n on the ring
     R* pst = cst + 2 * G::P1;                                        // [2][P1] phi^{n+1} (c kernel)
@@ -767,6 +874,37 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
     auto fslot = [&](int zg) { return sphi + ((unsigned)(zg - z0 + 2) % 5u) * G::P2; };
     auto islot = [&](int zg) { return (int)((unsigned)(zg - z0 + 1) % 3u); };
 
+    // tensor-map pulls of plane zg into stage (zg - z0) & 1 by the first warp:
+    // lane 0 arms the stage's barrier with the plane's bytes, then lane k < Q
+    // copies the box of link k (its y origin and e_z are fixed per block)
+    const int tl = threadIdx.x;                       // lane in the first warp (BX == 32)
+    const int tma_y = (TMA && tl < LP::Q) ? y0 - LP::ey(tl) : 0;
+    const int tma_ez = (TMA && tl < LP::Q) ? LP::ez(tl) : 0;
+    auto tma_issue = [&](int zg) {
+        if constexpr (TMA) {
+            if (threadIdx.y == 0) {
+                const int sidx = (zg - z0) & 1;
+                if (tl == 0) mbar_arrive_expect_tx(&bars[sidx], (unsigned)(TSTAGE * sizeof(R)));
+                __syncwarp();
+                if (tl < LP::Q) {
+                    int zs = zg - tma_ez;
+                    zs = zs < 0 ? zs + P.nz : (zs >= P.nz ? zs - P.nz : zs);
+                    tma_load_4d(tst + (sidx * LP::Q + tl) * BOXE, tmap, x0 - 4, tma_y, zs, tl, &bars[sidx]);
+                }
+            }
+        }
+    };
+    bool tma_late = false;           // a wait ran out (reported through err)
+    if constexpr (TMA) {
+        if (G::tid() == 0) {
+            mbar_init(&bars[0], 1);
+            mbar_init(&bars[1], 1);
+            fence_proxy_async();
+        }
+        __syncwarp();                // the first warp issues right after the initialisation
+        tma_issue(z0);
+    }
+
     for (int zg = z0 - 2; zg <= z0 + 1; ++zg) async_phi_plane<L, G>(P, phi_n, fslot(zg), zg, halo);
     fetch_ring(z0 - 1);
     cp_async_commit();
@@ -789,54 +927,79 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
             // prefetch for the next plane: phi plane z+3 into the slot of z-2, ring of z+2
             async_phi_plane<L, G>(P, phi_n, fslot(z + 3), z + 3, halo);
             fetch_ring(z + 2);
+            tma_issue(z + 1);        // its stage was last read by pull(z-1), done everywhere
         }
         cp_async_commit();
-        if (active_xy) pull_load<LP, SP, IS_PHI, WALLS, I>(K, fin, c_n, x, y, z, inside1 && z >= 1 && z + 1 < P.nz, st);
+        if (!TMA && active_xy)
+            pull_load<LP, SP, IS_PHI, WALLS, I>(K, fin, c_n, x, y, z, inside1 && z >= 1 && z + 1 < P.nz, st);
         ingredients(islot(z + 1), fslot(z), fslot(z + 1), fslot(z + 2), z + 1);
         __syncthreads();
+        if constexpr (TMA) {
+            const int sidx = (z - z0) & 1;
+            if (!mbar_wait(&bars[sidx], (unsigned)((z - z0) >> 1) & 1u)) tma_late = true;
+            const bool edge = active_xy && (x == 0 || x == P.nx - 1 || y == 0 || y == P.ny - 1);
+            const bool fix = __any_sync(0xffffffffu, edge);
+            if (active_xy)
+                tma_pull<LP, SP, BX, BY, IS_PHI, WALLS, I>(K, fin, c_n, x, y, z, tst + sidx * TSTAGE, edge, fix, st);
+        }
         if (active_xy)
-            pull_combine<LP, SP, BY, BX, IS_PHI, WALLS, I, U>(K, C, fout, sing + islot(z - 1) * G::P1,
+            pull_combine<LP, SP, BY, BX, IS_PHI, WALLS, I, U, TMA>(K, C, fout, sing + islot(z - 1) * G::P1,
                                                    sing + islot(z) * G::P1, sing + islot(z + 1) * G::P1,
                                                    fslot(z - 1), fslot(z), fslot(z + 1), sA + islot(z) * G::P1,
                                                    phi_np1, moment_out, st, macc);
     }
     cp_async_wait_all();
+    if constexpr (TMA) {
+        if (tma_late) {
+            // report, and give a copy still in flight a last bounded wait
+            // before the block's shared memory is released
+            atomicExch(err, 1);
+            mbar_wait(&bars[(z1 - 1 - z0) & 1], (unsigned)((z1 - 1 - z0) >> 1) & 1u);
+        }
+    }
 }
 
-template <class L, class SP, int BY, int BX = 32>
-constexpr size_t march_smem(bool is_phi) {
+template <class L, class SP, int BY, int BX = 32, class LH = L>
+constexpr size_t march_smem(bool is_phi, bool tma = false) {
     using G = Geo<L, BY, BX>;
     using R = typename SP::real;
     return sizeof(V4<R>) * G::NING * G::P1 + sizeof(R) * G::NPHI * G::P2 + sizeof(R) * 2 * G::P1 +
-           (is_phi ? sizeof(R) * G::NING * G::P1 : sizeof(R) * 2 * G::P1);
+           (is_phi ? sizeof(R) * G::NING * G::P1 : sizeof(R) * 2 * G::P1) +
+           (tma ? 2 * sizeof(R) * (is_phi ? L::Q : LH::Q) * (BX + 8) * BY + 16 : 0);
 }
 
 // ---- the two step kernels ----------------------------------------------------------
 
 // Block (bx, by, bz) marches the tile at (bx BX, by BY) over the planes
 // [bz zch, min((bz + 1) zch, nz)).
-template <class L, class SP, int BY, int MINB, bool WALLS, int BX = 32>
+// TMA: pulls through the tensor map tmap of the input populations (see
+// tma_pull); err is set if a copy never lands.
+template <class L, class SP, int BY, int MINB, bool WALLS, int BX = 32, bool TMA = false>
 __global__ void __launch_bounds__(BX * BY, MINB)
 k_phi_step(const KParams K, const typename SP::store_t* __restrict__ gin,
            typename SP::store_t* __restrict__ gout, const typename SP::real* __restrict__ phi_n,
-           const typename SP::real* __restrict__ c_n, typename SP::real* __restrict__ phi_np1, int zch) {
+           const typename SP::real* __restrict__ c_n, typename SP::real* __restrict__ phi_np1, int zch,
+           const __grid_constant__ CUtensorMap tmap, int* err) {
     MassAcc<typename SP::real> macc{0, 0};
     const int z0 = blockIdx.z * zch;
-    march<L, SP, BY, true, WALLS, BX>(K, gin, gout, phi_n, nullptr, c_n, phi_np1, macc, blockIdx.x * BX,
-                                      blockIdx.y * BY, z0, min(z0 + zch, K.P.nz));
+    march<L, SP, BY, true, WALLS, BX, long long, L, true, TMA>(K, gin, gout, phi_n, nullptr, c_n, phi_np1, macc,
+                                                               blockIdx.x * BX, blockIdx.y * BY, z0,
+                                                               min(z0 + zch, K.P.nz), &tmap, err);
 }
 
-template <class L, class SP, int BY, int MINB, bool WALLS, int BX = 32, class LH = L>
+template <class L, class SP, int BY, int MINB, bool WALLS, int BX = 32, class LH = L, bool TMA = false>
 __global__ void __launch_bounds__(BX * BY, MINB)
 k_c_step(const KParams K, const typename SP::store_t* __restrict__ hin,
          typename SP::store_t* __restrict__ hout, const typename SP::real* __restrict__ phi_n,
          const typename SP::real* __restrict__ phi_np1, const typename SP::real* __restrict__ c_n,
-         typename SP::real* __restrict__ c_np1, double* __restrict__ mass_partials, int zch) {
+         typename SP::real* __restrict__ c_np1, double* __restrict__ mass_partials, int zch,
+         const __grid_constant__ CUtensorMap tmap, int* err) {
     using G = Geo<L, BY, BX>;
     MassAcc<typename SP::real> macc{0, 0};
     const int z0 = blockIdx.z * zch;
-    march<L, SP, BY, false, WALLS, BX, long long, LH>(K, hin, hout, phi_n, phi_np1, c_n, c_np1, macc,
-                                                      blockIdx.x * BX, blockIdx.y * BY, z0, min(z0 + zch, K.P.nz));
+    march<L, SP, BY, false, WALLS, BX, long long, LH, true, TMA>(K, hin, hout, phi_n, phi_np1, c_n, c_np1, macc,
+                                                                 blockIdx.x * BX, blockIdx.y * BY, z0,
+                                                                 min(z0 + zch, K.P.nz), &tmap, err);
     if (mass_partials)
         block_mass_out<G::NT>(macc, mass_partials,
                               blockIdx.x + gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z));

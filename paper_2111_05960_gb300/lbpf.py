@@ -86,6 +86,7 @@ def load() -> ctypes.CDLL:
         "lbpf_batch_tile": [_vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32), _dp],
         "lbpf_batch_set_tile": [_vp, ctypes.c_int32, ctypes.c_int32],
         "lbpf_fp64_fma_rate": [_vp, _dp],
+        "lbpf_pull_path": [_vp, ctypes.POINTER(ctypes.c_int32)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -103,7 +104,8 @@ def exported_symbols():
             "lbpf_get_fields", "lbpf_get_populations", "lbpf_get_step", "lbpf_destroy",
             "lbpf_last_error", "lbpf_lattice_info", "lbpf_mass_noalloc", "lbpf_solute_mass",
             "lbpf_create_batch", "lbpf_batch_get_fields", "lbpf_batch_solute_mass",
-            "lbpf_adjoint_step", "lbpf_batch_tile", "lbpf_batch_set_tile", "lbpf_fp64_fma_rate"]
+            "lbpf_adjoint_step", "lbpf_batch_tile", "lbpf_batch_set_tile", "lbpf_fp64_fma_rate",
+            "lbpf_pull_path"]
 
 
 def _check(status: int, ctx=None):
@@ -273,6 +275,13 @@ def lbpf_adjoint_step(ctx, dL_dphi=None, dL_dc=None, dL_dphi0=None, dL_dc0=None,
     _check(load().lbpf_adjoint_step(ctx, _ptr(dL_dphi)[0], _ptr(dL_dc)[0], _ptr(dL_dphi0)[0],
                                     _ptr(dL_dc0)[0], int(ptr_is_device), out.ctypes.data_as(_dp)), ctx)
     return out
+
+
+def lbpf_pull_path(ctx) -> int:
+    """1 if the step kernels pull the populations through tensor maps, else 0."""
+    v = ctypes.c_int32()
+    _check(load().lbpf_pull_path(ctx, ctypes.byref(v)), ctx)
+    return int(v.value)
 
 
 def lbpf_fp64_fma_rate(cuda_stream=None) -> float:

@@ -108,6 +108,7 @@ def test_null_arguments(lib):
     assert lib.lbpf_create(ctypes.byref(p), None, None, 0, None, None) == L.LBPF_EINVAL
     assert lib.lbpf_step(None, 1) == L.LBPF_EINVAL
     assert lib.lbpf_mass(None, None, None) == L.LBPF_EINVAL
+    assert lib.lbpf_pull_path(None, None) == L.LBPF_EINVAL
     assert lib.lbpf_destroy(None) == L.LBPF_OK
     assert "NULL" in L.lbpf_last_error(None) or "ctx" in L.lbpf_last_error(None)
 
