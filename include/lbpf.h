@@ -240,7 +240,8 @@ lbpf_status lbpf_lattice_info(int32_t lattice, int32_t *q, int32_t *e, double *w
  * counter term on and off, ...), stepped together: each kernel phase is one
  * persistent launch over a flat list of row-marched tiles (BX columns x ROWS
  * rows, the shape picked by an autotuner at creation, see lbpf_batch_tile) of
- * all instances, so the work is balanced whatever the size mix.  p[i], phi0[i],
+ * all periodic instances, and one more over those of the instances with a
+ * bounce-back axis (if any), so the work is balanced whatever the size mix.  p[i], phi0[i],
  * c0[i] describe instance i exactly as for lbpf_create (each with its own
  * sizes, walls and parameters); all instances must be D2Q9 with the same
  * precision, mass_every = 0, checkpoint_every = 0, h_lattice = h_eq_alt =

@@ -25,31 +25,53 @@ struct BatchTileImpl {
     static constexpr size_t smem_phi = batch_smem<SP, BX, ROWS>(true);
     static constexpr size_t smem_c = batch_smem<SP, BX, ROWS>(false);
 
-    static lbpf_status prepare(lbpf_ctx* ctx) {
-        LBPF_CUDA(ctx, cudaFuncSetAttribute(k_batch_step<SP, true, BX, ROWS>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_phi));
-        LBPF_CUDA(ctx, cudaFuncSetAttribute(k_batch_step<SP, false, BX, ROWS>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
-        int sms = 0, occ_phi = 0, occ_c = 0;
-        LBPF_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
-        LBPF_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_phi, k_batch_step<SP, true, BX, ROWS>, BX,
-                                                                     smem_phi));
-        LBPF_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_c, k_batch_step<SP, false, BX, ROWS>, BX,
-                                                                     smem_c));
-        const int occ = std::max(1, std::min(occ_phi, occ_c));
-        ctx->persist_blocks = std::max(1, std::min(ctx->ntiles, sms * occ));
+    template <bool IS_PHI, bool W>
+    static constexpr auto kern() { return k_batch_step<SP, IS_PHI, BX, ROWS, W>; }
+
+    // resident blocks of one kernel (its shared memory and launch bounds)
+    template <bool IS_PHI, bool W>
+    static lbpf_status occupancy(lbpf_ctx* ctx, int* blocks) {
+        const size_t smem = IS_PHI ? smem_phi : smem_c;
+        LBPF_CUDA(ctx, cudaFuncSetAttribute(kern<IS_PHI, W>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        LBPF_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern<IS_PHI, W>(), BX, smem));
         return LBPF_OK;
     }
+    static lbpf_status prepare(lbpf_ctx* ctx) {
+        int sms = 0, o[4] = {0, 0, 0, 0};
+        LBPF_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+        lbpf_status st;
+        if ((st = occupancy<true, false>(ctx, &o[0])) != LBPF_OK) return st;
+        if ((st = occupancy<false, false>(ctx, &o[1])) != LBPF_OK) return st;
+        if ((st = occupancy<true, true>(ctx, &o[2])) != LBPF_OK) return st;
+        if ((st = occupancy<false, true>(ctx, &o[3])) != LBPF_OK) return st;
+        ctx->persist_blocks = std::max(1, sms * std::max(1, std::min(o[0], o[1])));
+        ctx->persist_blocks_walls = std::max(1, sms * std::max(1, std::min(o[2], o[3])));
+        return LBPF_OK;
+    }
+    // the periodic instances' tiles [0, ntiles_periodic), then the walled ones'
     static void launch(lbpf_ctx* ctx, int cur, bool is_phi) {
         const int nxt = cur ^ 1;
-        if (is_phi)
-            k_batch_step<SP, true, BX, ROWS><<<ctx->persist_blocks, BX, smem_phi, ctx->stream>>>(
-                ctx->d_binst, ctx->d_tile_inst, ctx->ntiles, (const S*)ctx->g[cur], (S*)ctx->g[nxt],
-                (const R*)ctx->phi[cur], nullptr, (const R*)ctx->c[cur], (R*)ctx->phi[nxt]);
-        else
-            k_batch_step<SP, false, BX, ROWS><<<ctx->persist_blocks, BX, smem_c, ctx->stream>>>(
-                ctx->d_binst, ctx->d_tile_inst, ctx->ntiles, (const S*)ctx->h[cur], (S*)ctx->h[nxt],
-                (const R*)ctx->phi[cur], (const R*)ctx->phi[nxt], (const R*)ctx->c[cur], (R*)ctx->c[nxt]);
+        const int n0 = ctx->ntiles_periodic, n1 = ctx->ntiles;
+        auto go = [&](auto k, int t0, int t1, int grid) {
+            if (t1 <= t0) return;
+            const int blocks = std::min(grid, t1 - t0);
+            if (is_phi)
+                k<<<blocks, BX, smem_phi, ctx->stream>>>(ctx->d_binst, ctx->d_tile_inst, t0, t1, (const S*)ctx->g[cur],
+                                                        (S*)ctx->g[nxt], (const R*)ctx->phi[cur], nullptr,
+                                                        (const R*)ctx->c[cur], (R*)ctx->phi[nxt]);
+            else
+                k<<<blocks, BX, smem_c, ctx->stream>>>(ctx->d_binst, ctx->d_tile_inst, t0, t1, (const S*)ctx->h[cur],
+                                                      (S*)ctx->h[nxt], (const R*)ctx->phi[cur],
+                                                      (const R*)ctx->phi[nxt], (const R*)ctx->c[cur],
+                                                      (R*)ctx->c[nxt]);
+        };
+        if (is_phi) {
+            go(kern<true, false>(), 0, n0, ctx->persist_blocks);
+            go(kern<true, true>(), n0, n1, ctx->persist_blocks_walls);
+        } else {
+            go(kern<false, false>(), 0, n0, ctx->persist_blocks);
+            go(kern<false, true>(), n0, n1, ctx->persist_blocks_walls);
+        }
     }
 };
 
@@ -137,13 +159,19 @@ lbpf_status set_tile(lbpf_ctx* ctx, int t) {
     int tiles = 0;
     try {
         tile_inst.reserve((size_t)tiles_of(ctx, t));
-        for (int i = 0; i < ctx->nb; ++i) {
-            BatchInst& I = ctx->binst[i];
-            I.tiles_x = (I.K.P.nx + kBatchTiles[t].bx - 1) / kBatchTiles[t].bx;
-            const int ty = (I.K.P.ny + kBatchTiles[t].rows - 1) / kBatchTiles[t].rows;
-            I.tile_begin = tiles;
-            for (int k = 0; k < I.tiles_x * ty; ++k) tile_inst.push_back(i);
-            tiles += I.tiles_x * ty;
+        // the periodic instances first, then those with a bounce-back axis:
+        // each group is stepped by its own kernel
+        for (int pass = 0; pass < 2; ++pass) {
+            if (pass == 1) ctx->ntiles_periodic = tiles;
+            for (int i = 0; i < ctx->nb; ++i) {
+                BatchInst& I = ctx->binst[i];
+                if ((I.walls != 0) != (pass == 1)) continue;
+                I.tiles_x = (I.K.P.nx + kBatchTiles[t].bx - 1) / kBatchTiles[t].bx;
+                const int ty = (I.K.P.ny + kBatchTiles[t].rows - 1) / kBatchTiles[t].rows;
+                I.tile_begin = tiles;
+                for (int k = 0; k < I.tiles_x * ty; ++k) tile_inst.push_back(i);
+                tiles += I.tiles_x * ty;
+            }
         }
     } catch (...) {
         return fail(ctx, LBPF_ENOMEM, "host allocation failed");

@@ -1,12 +1,14 @@
 // Batched coupled phi-mu LBM step for many 2-D instances of uneven size
 // (parameter sweeps, counter term on and off) in one persistent launch per
-// kernel phase.
+// kernel phase and boundary kind (periodic instances, instances with a
+// bounce-back axis).
 //
 // Every instance keeps its own SoA layout ([k][y][x] populations, [y][x]
 // fields) inside shared concatenated buffers.  The instances are cut into
 // tiles of BX columns x ROWS rows; one flat list holds the tiles of all
-// instances, and a persistent grid (SMs x resident blocks) walks it
-// round-robin, so the work is balanced whatever the size mix.  A tile is
+// instances (the periodic ones first), and a persistent grid (SMs x resident
+// blocks) walks each part of it round-robin, so the work is balanced whatever
+// the size mix.  A tile is
 // processed by the same row-marching code as a single 2-D simulation (the
 // D2Q9R view: BX-long row segments, ROWS rows), with its instance's parameters
 // read from a device table.  The tile shape is chosen per batch by timing the
@@ -31,20 +33,36 @@ struct BatchInst {
 struct BatchTile {
     int bx, rows;
 };
-// Candidate tile shapes (BX threads per block, LBPF_BATCH_TPSM / BX resident
-// blocks).  The instance parameters are read from shared memory, so the
-// compiler keeps the link offsets and coefficients in registers: at 1024
-// threads per SM (64 registers) the kernels spill, at 768 (80 registers) they
-// do not; 768 is also the fastest of 512-1024 on the 384-instance sweep.
+// Candidate tile shapes (BX threads per block, resident blocks per SM from the
+// thread budget below).  The instance parameters are read from shared memory,
+// so the compiler keeps the link offsets and coefficients in registers.  The
+// periodic and the walled instances are stepped by separate launches of
+// kernels that hold one march each: the periodic kernel, the one the sweeps
+// use, is built for 896 threads per SM (72 registers) and ran 3.7% faster on
+// the 384-instance sweep than one kernel with both marches at 768 (80
+// registers); at 1024 (64 registers) it spills and is slower.  The walled
+// kernel keeps 768.
 constexpr BatchTile kBatchTiles[] = {{64, 16}, {64, 32}, {128, 16}, {128, 32}, {256, 16}};
 constexpr int kNumBatchTiles = sizeof(kBatchTiles) / sizeof(kBatchTiles[0]);
 #ifndef LBPF_BATCH_TPSM
-#define LBPF_BATCH_TPSM 768
+#define LBPF_BATCH_TPSM 896
 #endif
+#ifndef LBPF_BATCH_TPSM_WALLS
+#define LBPF_BATCH_TPSM_WALLS 768
+#endif
+// FP64 arithmetic needs twice the registers: 512 threads per SM (128 registers)
+#ifndef LBPF_BATCH_TPSM_F64
+#define LBPF_BATCH_TPSM_F64 512
+#endif
+constexpr int batch_minb(int bx, bool walls, bool f64) {
+    return (f64 ? LBPF_BATCH_TPSM_F64 : (walls ? LBPF_BATCH_TPSM_WALLS : LBPF_BATCH_TPSM)) / bx;
+}
 
-template <class SP, bool IS_PHI, int BX, int ROWS>
-__global__ void __launch_bounds__(BX, LBPF_BATCH_TPSM / BX)
-k_batch_step(const BatchInst* __restrict__ inst, const int* __restrict__ tile_inst, int ntiles,
+// Tiles t_begin <= t < t_end of the flat list, all of instances with (WALLS)
+// or without bounce-back axes.
+template <class SP, bool IS_PHI, int BX, int ROWS, bool WALLS>
+__global__ void __launch_bounds__(BX, batch_minb(BX, WALLS, sizeof(typename SP::real) == 8))
+k_batch_step(const BatchInst* __restrict__ inst, const int* __restrict__ tile_inst, int t_begin, int t_end,
              const typename SP::store_t* __restrict__ fin, typename SP::store_t* __restrict__ fout,
              const typename SP::real* __restrict__ phi_n, const typename SP::real* __restrict__ phi_np1,
              const typename SP::real* __restrict__ c_n, typename SP::real* __restrict__ moment_out) {
@@ -53,7 +71,7 @@ k_batch_step(const BatchInst* __restrict__ inst, const int* __restrict__ tile_in
     // stores) on every use inside the link loops
     __shared__ KParams sK;
     static_assert(sizeof(KParams) % 4 == 0, "copied as 32-bit words");
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    for (int t = t_begin + blockIdx.x; t < t_end; t += gridDim.x) {
         __syncthreads();   // the previous tile's shared memory is free
         const BatchInst& I = inst[tile_inst[t]];
         const int* src = reinterpret_cast<const int*>(&I.Km);
@@ -63,17 +81,12 @@ k_batch_step(const BatchInst* __restrict__ inst, const int* __restrict__ tile_in
         const int x0 = (lt % I.tiles_x) * BX;
         const int z0 = (lt / I.tiles_x) * ROWS;
         const long long po = I.pop_off, fo = I.fld_off;
-        const bool walls = I.walls != 0;
         __syncthreads();
         const typename SP::real* pn1 = phi_np1 ? phi_np1 + fo : nullptr;
         const int z1 = min(z0 + ROWS, sK.P.nz);
         MassAcc<typename SP::real> macc{0, 0};
-        if (walls)
-            march<D2Q9R, SP, 1, IS_PHI, true, BX, int, D2Q9R, false>(sK, fin + po, fout + po, phi_n + fo, pn1, c_n + fo,
-                                                                     moment_out + fo, macc, x0, 0, z0, z1);
-        else
-            march<D2Q9R, SP, 1, IS_PHI, false, BX, int, D2Q9R, false>(sK, fin + po, fout + po, phi_n + fo, pn1,
-                                                                      c_n + fo, moment_out + fo, macc, x0, 0, z0, z1);
+        march<D2Q9R, SP, 1, IS_PHI, WALLS, BX, int, D2Q9R, false>(sK, fin + po, fout + po, phi_n + fo, pn1, c_n + fo,
+                                                                  moment_out + fo, macc, x0, 0, z0, z1);
     }
 }
 

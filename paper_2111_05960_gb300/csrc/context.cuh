@@ -96,7 +96,9 @@ struct lbpf_ctx {
     lbpf::BatchInst* d_binst = nullptr;
     int* d_tile_inst = nullptr;
     int ntiles = 0;
-    int persist_blocks = 0;
+    int ntiles_periodic = 0;              // tiles of the instances without bounce-back axes (listed first)
+    int persist_blocks = 0;               // grid of the periodic kernels
+    int persist_blocks_walls = 0;         // grid of the walled kernels
     int btile = 0;                        // tile shape in use (index into lbpf::kBatchTiles)
     double btile_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // autotuner: ms per step of each shape
     int tile_capacity = 0;                // entries of d_tile_inst
