@@ -256,7 +256,7 @@ def batch_measurement(args, stream, hbm):
     return {"workload": "batch_2d_384_d2q9_fp32", "instances": 384, "nodes": nodes, "steps": args.batch_steps,
             "tile": {"shape": list(tile), "autotune_ms_per_step": dict(zip(["%dx%d" % t for t in L.BATCH_TILES], [float(v) for v in tune_ms]))},
             "ms_per_step": ms, "mlups": nodes / (ms * 1e-3) / 1e6, "bytes_per_node": bytes_node,
-            "achieved_gbs": gbs, "frac": gbs / hbm, "launch": "2 persistent launches per step, CUDA graph",
+            "achieved_gbs": gbs, "frac": gbs / hbm, "launch": "2 persistent launches per step (all 384 instances are periodic; walled instances would add 2), CUDA graph",
             "kernel_ms": {"k_batch_phi": k_phi / 10, "k_batch_c": k_c / 10}}
 
 
