@@ -380,11 +380,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
         : "memory");
     return done != 0;
 }
-// Bounded wait: each try suspends for a hardware-chosen time, and 2^20 tries
-// end well within a second.  false: the phase never completed.
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
+}
+// Bounded wait: gives up after about a second of the global timer (and in any
+// case after 2^20 rounds of 64 tries).  false: the phase never completed.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
-    for (int i = 0; i < (1 << 20); ++i)
-        if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (int round = 0; round < (1 << 20); ++round) {
+        for (int i = 0; i < 64; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > 1000000000ull) return false;
+    }
     return false;
 }
 // Box of a 4-D tensor map at coordinates (c0 innermost .. c3) into shared memory.
@@ -936,7 +946,9 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
         __syncthreads();
         if constexpr (TMA) {
             const int sidx = (z - z0) & 1;
-            if (!mbar_wait(&bars[sidx], (unsigned)((z - z0) >> 1) & 1u)) tma_late = true;
+            // after one wait has run out the block stops waiting (its results are
+            // flagged through err), so a broken copy costs about a second, not one per plane
+            if (!tma_late && !mbar_wait(&bars[sidx], (unsigned)((z - z0) >> 1) & 1u)) tma_late = true;
             const bool edge = active_xy && (x == 0 || x == P.nx - 1 || y == 0 || y == P.ny - 1);
             const bool fix = __any_sync(0xffffffffu, edge);
             if (active_xy)
