@@ -263,8 +263,8 @@ lbpf_status lbpf_create_batch(const lbpf_params *p, int32_t n, const double *con
 
 /* Tile shape of a batch's step kernels: each persistent block walks tiles of
  * *tile_x columns x *tile_rows rows (row segments marched along y).  At
- * creation the library times one step with each built shape (64x16, 64x32,
- * 128x16, 128x32, 256x16) on the batch itself and keeps the fastest; the shape
+ * creation the library times one step with each built shape (32x32, 32x64,
+ * 64x32, 64x64, 128x32) on the batch itself and keeps the fastest; the shape
  * changes the schedule only, never the results.  ms_per_step (optional, 5
  * doubles) receives the timed milliseconds per step of each shape in that
  * order.  Errors: EINVAL (NULL pointers, not a batch). */

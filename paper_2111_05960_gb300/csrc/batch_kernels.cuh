@@ -42,7 +42,7 @@ struct BatchTile {
 // the 384-instance sweep than one kernel with both marches at 768 (80
 // registers); at 1024 (64 registers) it spills and is slower.  The walled
 // kernel keeps 768.
-constexpr BatchTile kBatchTiles[] = {{64, 16}, {64, 32}, {128, 16}, {128, 32}, {256, 16}};
+constexpr BatchTile kBatchTiles[] = {{32, 32}, {32, 64}, {64, 32}, {64, 64}, {128, 32}};
 constexpr int kNumBatchTiles = sizeof(kBatchTiles) / sizeof(kBatchTiles[0]);
 #ifndef LBPF_BATCH_TPSM
 #define LBPF_BATCH_TPSM 896

@@ -214,7 +214,7 @@ def lbpf_batch_solute_mass(ctx, n: int) -> np.ndarray:
     return out
 
 
-BATCH_TILES = ((64, 16), (64, 32), (128, 16), (128, 32), (256, 16))
+BATCH_TILES = ((32, 32), (32, 64), (64, 32), (64, 64), (128, 32))
 
 
 def lbpf_batch_tile(ctx):
