@@ -6,6 +6,7 @@
 // each step.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -180,6 +181,25 @@ bool encode_pop_map(CUtensorMap* m, void* base, const StepParams& P, int q, int 
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Planes per block of a 3-D step kernel: tiles x-y tiles, nz planes, resident
+// blocks per wave, def the default chunk (see Impl::prepare).
+int pick_zch(long long tiles, int nz, long long resident, int def) {
+    auto waves = [&](int z) { return (double)(tiles * ((nz + z - 1) / z)) / (double)resident; };
+    if (waves(def) >= 3.0) return def;
+    int best = def;
+    double best_fill = -1.0;
+    for (int z : {8, 12, 16, 24}) {
+        const double W = waves(z);
+        if (W < 1.5) continue;
+        const double fill = W / std::ceil(W);
+        if (fill >= best_fill) {
+            best_fill = fill;
+            best = z;
+        }
+    }
+    return best;
+}
+
 // HS: h on the small lattice of L (D2Q5 / D3Q7) instead of L itself.
 template <class L, class SP, bool HS = false>
 struct Impl {
@@ -212,6 +232,56 @@ struct Impl {
     static lbpf_status prepare(lbpf_ctx* ctx) {
         ctx->zch_phi = ZCH;
         ctx->zch_c = ZCHC;
+        if constexpr (L::D == 3) {
+            // 3-D: planes per block.  Grids of at least 3 waves of resident blocks
+            // at the default chunk keep it; smaller ones take the chunk of 8, 12,
+            // 16 or 24 planes whose last wave is fullest among those with at
+            // least 1.5 waves (the longer on a tie): on GB300 128^3 went from
+            // 12.2 to 13.5 GLUPS (12 planes), 160^3 from 12.8 to 14.2 (8),
+            // 192^3 from 15.0 to 15.3 (16); 256^3 keeps 32.
+            int sms = 0, occ_phi = 0, occ_c = 0;
+            const bool w = walls(ctx);
+            LBPF_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+            LBPF_CUDA(ctx, cudaFuncSetAttribute(w ? kphi<true>() : kphi<false>(),
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_phi));
+            LBPF_CUDA(ctx, cudaFuncSetAttribute(w ? kc<true>() : kc<false>(),
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
+            LBPF_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_phi, w ? kphi<true>() : kphi<false>(),
+                                                                         BX * BY, smem_phi));
+            LBPF_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_c, w ? kc<true>() : kc<false>(),
+                                                                         BX * BYC, smem_c));
+            const StepParams& P = ctx->kpm.P;
+            const long long tx = (P.nx + BX - 1) / BX;
+            ctx->zch_phi = pick_zch(tx * ((P.ny + BY - 1) / BY), P.nz, (long long)sms * std::max(1, occ_phi), ZCH);
+            ctx->zch_c = pick_zch(tx * ((P.ny + BYC - 1) / BYC), P.nz, (long long)sms * std::max(1, occ_c), ZCHC);
+        }
+        if constexpr (L::D == 2) {
+            // 2-D: rows per block.  The shortest chunk of 4, 8, 16, 32 rows whose
+            // grid fits in one wave of resident blocks (every block runs at once,
+            // no tail), else the default; on GB300 this took the 512^2 disc from
+            // 6.6 to 10.2 GLUPS, the 1024^2 slice of Sec. 5 from 15.2 to 17.5 and
+            // 2048^2 from 26.0 to 27.1 (4096^2 keeps 16 rows: 30.8).
+            int sms = 0, occ_phi = 0, occ_c = 0;
+            const bool w = walls(ctx);
+            LBPF_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+            LBPF_CUDA(ctx, cudaFuncSetAttribute(w ? kphi<true>() : kphi<false>(),
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_phi));
+            LBPF_CUDA(ctx, cudaFuncSetAttribute(w ? kc<true>() : kc<false>(),
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
+            LBPF_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_phi, w ? kphi<true>() : kphi<false>(),
+                                                                         BX * BY, smem_phi));
+            LBPF_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_c, w ? kc<true>() : kc<false>(),
+                                                                         BX * BYC, smem_c));
+            const long long resident = (long long)sms * std::max(1, std::min(occ_phi, occ_c));
+            const StepParams& P = ctx->kpm.P;     // rows are the planes of the marching view
+            const long long tiles_x = (P.nx + BX - 1) / BX;
+            for (int rows : {4, 8, 16, 32}) {
+                if (tiles_x * ((P.nz + rows - 1) / rows) <= resident) {
+                    ctx->zch_phi = ctx->zch_c = rows;
+                    break;
+                }
+            }
+        }
         LBPF_CUDA(ctx, cudaFuncSetAttribute(kphi<true>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_phi));
         LBPF_CUDA(ctx, cudaFuncSetAttribute(kc<true>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
         LBPF_CUDA(ctx, cudaFuncSetAttribute(kphi<false>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_phi));
