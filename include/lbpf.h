@@ -209,13 +209,14 @@ lbpf_status lbpf_get_populations(lbpf_ctx *ctx, double *g, double *h, int32_t pt
 lbpf_status lbpf_step_timed(lbpf_ctx *ctx, int64_t nsteps, double *kernel_ms);
 
 /* How the context's step kernels read the populations they pull:
- * *tensor_maps = 1 when the copy engine brings each plane's population rows
- * into shared memory through tensor maps of the context's buffers, 0 when
- * every thread loads its own.  The tensor-map form is opt-in: the environment
- * variable LBPF_TMA=1 at creation, FP32 storage on D3Q19, every axis periodic,
- * nx a multiple of 4 and at least 40.  Its results are bit-identical to the
- * load form; it is about twice slower on GB300 (one copy request per link,
- * tile and plane), so it is not the default.  Needs no GPU work.
+ * *tensor_maps = 1 when the copy engine brings each plane's rows of the links
+ * with e_x = 0 into shared memory through tensor maps of the context's buffers
+ * (the threads load the other links themselves), 0 when every thread loads all
+ * of its own.  The tensor-map form is opt-in: the environment variable
+ * LBPF_TMA=1 at creation, FP32 storage on D3Q19, every axis periodic, nx a
+ * multiple of 4 and at least 32.  Its results are bit-identical to the load
+ * form; it is slower on GB300 (1.31 against 1.02 ms per 256^3 step), so it is
+ * not the default.  Needs no GPU work.
  * Errors: EINVAL (ctx or tensor_maps NULL). */
 lbpf_status lbpf_pull_path(const lbpf_ctx *ctx, int32_t *tensor_maps);
 

@@ -120,7 +120,7 @@ namespace {
 #define LBPF_MINB3_HS 4
 #endif
 #ifndef LBPF_MINB3_TMA
-#define LBPF_MINB3_TMA 5
+#define LBPF_MINB3_TMA 6
 #endif
 // Increment per corrected node of the mass correction: ~100 ulps of an FP32
 // value near 1, so that each node's rounding is ~1% of the increment.
@@ -220,8 +220,8 @@ struct Impl {
     static constexpr size_t smem_phi_t = march_smem<ML, SP, BY, BX, MLH>(true, true);
     static constexpr size_t smem_c_t = march_smem<ML, SP, BYC, BX, MLH>(false, true);
     static_assert(smem_phi_t <= 227 * 1024 && smem_c_t <= 227 * 1024, "a block's shared memory");
-    // the TMA kernels' stages take ~24 KB more shared memory per block: 5
-    // resident blocks, so they are compiled for 5
+    // the TMA kernels' stages take ~9 KB more shared memory per block (6 blocks
+    // of the FP32 D3Q19 tile still fit)
     template <bool W, bool T = false>
     static constexpr auto kphi() { return k_phi_step<ML, SP, BY, T ? LBPF_MINB3_TMA : MINB, W, BX, T>; }
     template <bool W, bool T = false>
@@ -294,18 +294,19 @@ struct Impl {
         }
         return LBPF_OK;
     }
-    // maps of the context's g and h buffers for the TMA kernels; false: this
-    // context pulls with loads (walls, 16-bit or FP64 storage, rows whose byte
-    // stride is not a multiple of 16, or a grid narrower than one box)
+    // maps of the context's g and h buffers for the TMA kernels (boxes of BX x
+    // BY values); false: this context pulls with loads only (walls, 16-bit or
+    // FP64 storage, rows whose byte stride is not a multiple of 16, or a grid
+    // narrower than one box)
     static bool setup_tensor_maps(lbpf_ctx* ctx) {
         if constexpr (!TMA_OK) {
             return false;
         } else {
             const StepParams& P = ctx->kpm.P;
-            if (walls(ctx) || P.sx != P.nx || P.nx % 4 != 0 || P.nx < BX + 8) return false;
+            if (walls(ctx) || P.sx != P.nx || P.nx % 4 != 0 || P.nx < BX) return false;
             for (int i = 0; i < 2; ++i) {
-                if (!encode_pop_map(&ctx->gmap[i], ctx->g[i], P, ML::Q, BX + 8, BY)) return false;
-                if (!encode_pop_map(&ctx->hmap[i], ctx->h[i], P, MLH::Q, BX + 8, BYC)) return false;
+                if (!encode_pop_map(&ctx->gmap[i], ctx->g[i], P, ML::Q, BX, BY)) return false;
+                if (!encode_pop_map(&ctx->hmap[i], ctx->h[i], P, MLH::Q, BX, BYC)) return false;
             }
             return true;
         }
@@ -760,8 +761,9 @@ lbpf_status lbpf_create(const lbpf_params* p, const double* phi0, const double* 
     std::memset(&ctx->nomap, 0, sizeof(ctx->nomap));
     {
         // the tensor-map pulls are opt-in (LBPF_TMA=1): bit-identical to the
-        // load path, but twice slower at 256^3 (one copy-engine request per
-        // link and plane: 19 boxes of 4 rows per 32 x 4 tile and plane)
+        // load path, but slower at 256^3 (1.31 against 1.02 ms per step: the
+        // copy engine does not deliver the 9 boxes per tile and plane as fast
+        // as the threads load the same rows)
         const char* tma = getenv("LBPF_TMA");
         ctx->tma = tma && strcmp(tma, "1") == 0 && ops->setup_tensor_maps(ctx);
     }

@@ -590,7 +590,29 @@ struct PullState {
     const R* srow;   // tensor-map pulls: this thread's column of the stage (see tma_pull)
 };
 
-template <class L, class SP, bool IS_PHI, bool WALLS, typename I>
+// Links of L along which x does not change (e_x = 0): their upstream rows are
+// the tile's own columns, which the tensor-map form copies whole.
+template <class L>
+__host__ __device__ constexpr int ex0_count() {
+    int n = 0;
+    for (int k = 0; k < L::Q; ++k) n += L::ex(k) == 0 ? 1 : 0;
+    return n;
+}
+template <class L>
+__host__ __device__ constexpr int ex0_slot(int k) {      // rank of link k among them
+    int n = 0;
+    for (int j = 0; j < k; ++j) n += L::ex(j) == 0 ? 1 : 0;
+    return n;
+}
+template <class L>
+__host__ __device__ constexpr int ex0_link(int j) {      // the j-th of them
+    for (int k = 0; k < L::Q; ++k)
+        if (L::ex(k) == 0 && j-- == 0) return k;
+    return 0;
+}
+
+// SKIP0: leave the links with e_x = 0 out (the tensor-map form brings them).
+template <class L, class SP, bool IS_PHI, bool WALLS, typename I, bool SKIP0 = false>
 __device__ __forceinline__ void pull_load(const KParams& K, const typename SP::store_t* __restrict__ fin,
                                           const typename SP::real* __restrict__ c_n, int x, int y, int z, bool fast,
                                           PullState<L, SP, IS_PHI, WALLS, I>& st) {
@@ -604,7 +626,8 @@ __device__ __forceinline__ void pull_load(const KParams& K, const typename SP::s
     if (fast) {
         const typename SP::store_t* base = fin + xi;
 #pragma unroll
-        for (int k = 0; k < L::Q; ++k) st.old[k] = SP::load(byte_add(base, link_src<I>(K, k)), 0, R(0));
+        for (int k = 0; k < L::Q; ++k)
+            if (!SKIP0 || L::ex(k) != 0) st.old[k] = SP::load(byte_add(base, link_src<I>(K, k)), 0, R(0));
         return;
     }
     // source offsets indexed by e + 1: e = +1 reads the node at -1, e = -1 the node at +1
@@ -633,6 +656,7 @@ __device__ __forceinline__ void pull_load(const KParams& K, const typename SP::s
     }
 #pragma unroll
     for (int k = 0; k < L::Q; ++k) {
+        if (SKIP0 && L::ex(k) == 0) continue;
         const bool wall = WALLS && (WX[L::ex(k) + 1] || WY[L::ey(k) + 1] || WZ[L::ez(k) + 1]);
         const I si = SZ[L::ez(k) + 1] + SY[L::ey(k) + 1] + SX[L::ex(k) + 1];
         // half-way bounce-back: f_k(x, n+1) = f*_{opp k}(x, n)
@@ -643,51 +667,46 @@ __device__ __forceinline__ void pull_load(const KParams& K, const typename SP::s
     }
 }
 
-// The slots of the links whose upstream node lies across an x or y face:
-// the wrapped node's value.  Out of line, so that the registers it needs do
-// not weigh on the march (only threads on those faces call it).
+// The slots of the e_x = 0 links whose upstream row lies across a y face: the
+// wrapped row's value.  Out of line, so that the registers it needs do not
+// weigh on the march (only threads on those faces call it).
 template <class L, int BOXE, typename R>
-__device__ __noinline__ void tma_fix_edges(const R* __restrict__ fin, int nx, int ny, int nz, long long sx,
-                                           long long sxy, long long ns, int x, int y, int z, R* row) {
+__device__ __noinline__ void tma_fix_edges(const R* __restrict__ fin, int ny, int nz, long long sx, long long sxy,
+                                           long long ns, int x, int y, int z, R* col) {
 #pragma unroll 1
     for (int k = 0; k < L::Q; ++k) {
-        const int ex = L::ex(k), ey = L::ey(k);
-        const int ux = x - ex, uy = y - ey;
-        if (ux < 0 || ux >= nx || uy < 0 || uy >= ny) {
-            const int xs = ux < 0 ? ux + nx : (ux >= nx ? ux - nx : ux);
-            const int ys = uy < 0 ? uy + ny : (uy >= ny ? uy - ny : uy);
+        if (L::ex(k) != 0) continue;
+        const int uy = y - L::ey(k);
+        if (uy < 0 || uy >= ny) {
+            const int ys = uy < 0 ? uy + ny : uy - ny;
             int zs = z - L::ez(k);
             zs = zs < 0 ? zs + nz : (zs >= nz ? zs - nz : zs);
-            row[k * BOXE - ex] = fin[k * ns + zs * sxy + ys * sx + xs];
+            col[ex0_slot<L>(k) * BOXE] = fin[k * ns + zs * sxy + ys * sx + x];
         }
     }
 }
 
-// Pull of plane z from the rows the copy engine placed in shared memory (the
-// tensor-map path: all axes periodic, FP32 storage).  Link k's box holds rows
-// y0 - ey .. y0 - ey + BY - 1 of plane z - ez (wrapped), columns x0 - 4 ..
-// x0 + BX + 3, so the thread at (tx, ty) finds its upstream value at row ty,
-// column tx + 4 - ex, a slot no other thread reads; the collision reads it
-// there.  A box row or column outside the grid was filled with zeros: the
-// threads on the grid's x or y faces (`edge`) overwrite those slots with the
-// wrapped node's value.  `fix`: some lane of the warp is such a thread.
+// The e_x = 0 pulls of plane z, from the boxes the copy engine placed in shared
+// memory (the tensor-map form: all axes periodic, FP32 storage; the other
+// links are loaded by pull_load).  The box of the j-th such link k holds rows
+// y0 - ey .. y0 - ey + BY - 1 of plane z - ez (wrapped), columns x0 .. x0 + BX
+// - 1, so the thread at (tx, ty) finds its upstream value at row ty, column tx,
+// a slot no other thread reads; the collision reads it there.  A box row
+// outside the grid was filled with zeros: the threads on the grid's y faces
+// (`edge`) overwrite those slots with the wrapped row's value.  `fix`: some
+// lane of the warp is such a thread.
 template <class L, class SP, int BX, int BY, bool IS_PHI, bool WALLS, typename I>
-__device__ __forceinline__ void tma_pull(const KParams& K, const typename SP::store_t* __restrict__ fin,
-                                         const typename SP::real* __restrict__ c_n, int x, int y, int z,
-                                         typename SP::real* stage, bool edge, bool fix,
+__device__ __forceinline__ void tma_pull(const KParams& K, const typename SP::store_t* __restrict__ fin, int x,
+                                         int y, int z, typename SP::real* stage, bool edge, bool fix,
                                          PullState<L, SP, IS_PHI, WALLS, I>& st) {
     using R = typename SP::real;
-    constexpr int TXW = BX + 8, BOXE = TXW * BY;
+    constexpr int BOXE = BX * BY;
     const StepParams& P = K.P;
-    const I xi = (I)z * (I)P.sxy + (I)y * P.sx + x;
-    st.xi = xi;
-    st.wallmask = 0u;
-    st.cx = IS_PHI ? R(0) : c_n[xi];
-    R* row = stage + threadIdx.y * TXW + threadIdx.x + 4;
-    st.srow = row;
+    R* col = stage + threadIdx.y * BX + threadIdx.x;
+    st.srow = col;
     if (fix) {
-        if (edge) tma_fix_edges<L, BOXE>(fin, P.nx, P.ny, P.nz, (long long)P.sx, (long long)P.sxy, (long long)P.NS,
-                                         x, y, z, row);
+        if (edge) tma_fix_edges<L, BOXE>(fin, P.ny, P.nz, (long long)P.sx, (long long)P.sxy, (long long)P.NS, x, y, z,
+                                         col);
         // these generic writes come before the copy engine refills the stage
         fence_proxy_async();
     }
@@ -730,8 +749,10 @@ __device__ __forceinline__ void pull_combine(const KParams& K, const Coef<typena
     if (!IS_PHI) {
         // rest population of h: h*_0 = (1 - w_h) h_0 + w_h h^eq_0 (H_0 = 0)
         const R heq0 = st.cx - R(L::DEN - L::m(0)) * i0[c1].a;   // h^eq_0 = c - (1 - w_0) P
-        const R old0 = TS ? st.srow[0] : st.old[0];
-        v[0] = keep * (SP::deviation ? old0 + heq0 : old0) + om * heq0;
+        const R old0 = TS ? st.srow[0] : st.old[0];   // link 0 (rest, e_x = 0) is slot 0
+        // the contraction is written out, so that it does not depend on where
+        // the operands come from (loads, shared memory)
+        v[0] = fma(keep, SP::deviation ? old0 + heq0 : old0, om * heq0);
         sum = v[0];
         if (!hold) SP::store(byte_add(out, link_base<I>(K, 0)), 0, v[0], R(0));
     }
@@ -744,13 +765,13 @@ __device__ __forceinline__ void pull_combine(const KParams& K, const Coef<typena
         const R* fk = L::ez(k) > 0 ? fm : (L::ez(k) < 0 ? fp : f0);
         const V4<R> g = wall ? i0[c1] : ik[c1 - L::ex(k) - G::X1 * L::ey(k)];
         const R sgn = wall ? R(-1) : R(1);
-        R f_old = TS ? st.srow[k * (BX + 8) * BY - L::ex(k)] : st.old[k];
+        R f_old = (TS && L::ex(k) == 0) ? st.srow[ex0_slot<L>(k) * BX * BY] : st.old[k];
         if (SP::deviation) {
             const R ref = IS_PHI ? wk * (wall ? f0[c2] : fk[c2 - L::ex(k) - G::X2 * L::ey(k)]) : mk * g.a;
             f_old += ref;
         }
         const R a = IS_PHI ? g.a : om * g.a;
-        const R val = keep * f_old + mk * (a + sgn * edot<L>(k, g.b, g.c, g.d));
+        const R val = fma(keep, f_old, mk * (a + sgn * edot<L>(k, g.b, g.c, g.d)));
         v[k] = val;
         if (IS_PHI || sizeof(R) == 8) {
             sum += val;          // FP64: a plain sum is unbiased far below FP64 resolution
@@ -836,9 +857,10 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
                   "tensor-map pulls: FP32 storage, periodic 3-D tiles");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // tensor-map stages first (128-byte aligned boxes), then their two barriers
-    constexpr int TXW = BX + 8, BOXE = TXW * BY;
-    constexpr int TSTAGE = TMA ? LH::Q * BOXE : 0;               // elements of one stage
-    R* tst = reinterpret_cast<R*>(smem_raw);                         // [2][LH::Q][BY][TXW]
+    constexpr int Q0 = ex0_count<LH>();                              // links with e_x = 0
+    constexpr int BOXE = BX * BY;
+    constexpr int TSTAGE = TMA ? Q0 * BOXE : 0;                      // elements of one stage
+    R* tst = reinterpret_cast<R*>(smem_raw);                         // [2][Q0][BY][BX]
     uint64_t* bars = reinterpret_cast<uint64_t*>(tst + 2 * TSTAGE);   // [2] (TMA only)
     unsigned char* rest = smem_raw + (TMA ? 2 * TSTAGE * sizeof(R) + 16 : 0);
     V4<R>* sing = reinterpret_cast<V4<R>*>(rest);                    // [NING][P1]
@@ -885,21 +907,23 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
     auto islot = [&](int zg) { return (int)((unsigned)(zg - z0 + 1) % 3u); };
 
     // tensor-map pulls of plane zg into stage (zg - z0) & 1 by the first warp:
-    // lane 0 arms the stage's barrier with the plane's bytes, then lane k < Q
-    // copies the box of link k (its y origin and e_z are fixed per block)
+    // lane 0 arms the stage's barrier with the plane's bytes, then lane j < Q0
+    // copies the box of the j-th e_x = 0 link (its y origin and e_z are fixed
+    // per block)
     const int tl = threadIdx.x;                       // lane in the first warp (BX == 32)
-    const int tma_y = (TMA && tl < LP::Q) ? y0 - LP::ey(tl) : 0;
-    const int tma_ez = (TMA && tl < LP::Q) ? LP::ez(tl) : 0;
+    const int tma_k = (TMA && tl < Q0) ? ex0_link<LP>(tl) : 0;
+    const int tma_y = y0 - LP::ey(tma_k);
+    const int tma_ez = LP::ez(tma_k);
     auto tma_issue = [&](int zg) {
         if constexpr (TMA) {
             if (threadIdx.y == 0) {
                 const int sidx = (zg - z0) & 1;
                 if (tl == 0) mbar_arrive_expect_tx(&bars[sidx], (unsigned)(TSTAGE * sizeof(R)));
                 __syncwarp();
-                if (tl < LP::Q) {
+                if (tl < Q0) {
                     int zs = zg - tma_ez;
                     zs = zs < 0 ? zs + P.nz : (zs >= P.nz ? zs - P.nz : zs);
-                    tma_load_4d(tst + (sidx * LP::Q + tl) * BOXE, tmap, x0 - 4, tma_y, zs, tl, &bars[sidx]);
+                    tma_load_4d(tst + (sidx * Q0 + tl) * BOXE, tmap, x0, tma_y, zs, tma_k, &bars[sidx]);
                 }
             }
         }
@@ -940,8 +964,8 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
             tma_issue(z + 1);        // its stage was last read by pull(z-1), done everywhere
         }
         cp_async_commit();
-        if (!TMA && active_xy)
-            pull_load<LP, SP, IS_PHI, WALLS, I>(K, fin, c_n, x, y, z, inside1 && z >= 1 && z + 1 < P.nz, st);
+        if (active_xy)
+            pull_load<LP, SP, IS_PHI, WALLS, I, TMA>(K, fin, c_n, x, y, z, inside1 && z >= 1 && z + 1 < P.nz, st);
         ingredients(islot(z + 1), fslot(z), fslot(z + 1), fslot(z + 2), z + 1);
         __syncthreads();
         if constexpr (TMA) {
@@ -949,10 +973,10 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
             // after one wait has run out the block stops waiting (its results are
             // flagged through err), so a broken copy costs about a second, not one per plane
             if (!tma_late && !mbar_wait(&bars[sidx], (unsigned)((z - z0) >> 1) & 1u)) tma_late = true;
-            const bool edge = active_xy && (x == 0 || x == P.nx - 1 || y == 0 || y == P.ny - 1);
+            const bool edge = active_xy && (y == 0 || y == P.ny - 1);
             const bool fix = __any_sync(0xffffffffu, edge);
             if (active_xy)
-                tma_pull<LP, SP, BX, BY, IS_PHI, WALLS, I>(K, fin, c_n, x, y, z, tst + sidx * TSTAGE, edge, fix, st);
+                tma_pull<LP, SP, BX, BY, IS_PHI, WALLS, I>(K, fin, x, y, z, tst + sidx * TSTAGE, edge, fix, st);
         }
         if (active_xy)
             pull_combine<LP, SP, BY, BX, IS_PHI, WALLS, I, U, TMA>(K, C, fout, sing + islot(z - 1) * G::P1,
@@ -977,7 +1001,7 @@ constexpr size_t march_smem(bool is_phi, bool tma = false) {
     using R = typename SP::real;
     return sizeof(V4<R>) * G::NING * G::P1 + sizeof(R) * G::NPHI * G::P2 + sizeof(R) * 2 * G::P1 +
            (is_phi ? sizeof(R) * G::NING * G::P1 : sizeof(R) * 2 * G::P1) +
-           (tma ? 2 * sizeof(R) * (is_phi ? L::Q : LH::Q) * (BX + 8) * BY + 16 : 0);
+           (tma ? 2 * sizeof(R) * (is_phi ? ex0_count<L>() : ex0_count<LH>()) * BX * BY + 16 : 0);
 }
 
 // ---- the two step kernels ----------------------------------------------------------
