@@ -837,6 +837,11 @@ __device__ __forceinline__ void block_mass_out(const MassAcc<R>& m, double* __re
 // One z-marching pass of either kernel over the planes z0 <= z < z1 of the tile
 // at (x0, y0).  The composition kernel also adds the exact mass of the
 // populations it writes to macc.
+// Stages of the tensor-map ring: the copies run NST - 1 planes ahead.
+#ifndef LBPF_TMA_STAGES
+#define LBPF_TMA_STAGES 2
+#endif
+
 // TMA: the pulls come from tensor-map copies (tmap: the 4-D map of fin, see
 // tma_pull); a copy that never lands sets *err after a bounded wait.
 template <class L, class SP, int BY, bool IS_PHI, bool WALLS, int BX = 32, typename I = long long,
@@ -861,8 +866,13 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
     constexpr int BOXE = BX * BY;
     constexpr int TSTAGE = TMA ? Q0 * BOXE : 0;                      // elements of one stage
     R* tst = reinterpret_cast<R*>(smem_raw);                         // [2][Q0][BY][BX]
-    uint64_t* bars = reinterpret_cast<uint64_t*>(tst + 2 * TSTAGE);   // [2] (TMA only)
-    unsigned char* rest = smem_raw + (TMA ? 2 * TSTAGE * sizeof(R) + 16 : 0);
+    constexpr int NST = LBPF_TMA_STAGES;                             // stages in the ring
+    uint64_t* bars = reinterpret_cast<uint64_t*>(tst + NST * TSTAGE);  // [NST] (TMA only)
+    // the rest starts on a 128-byte boundary after the stages and barriers
+    unsigned char* rest = smem_raw + (TMA ? (NST * TSTAGE * sizeof(R) + 8 * NST + 127) / 128 * 128 : 0);
+    // plane zg uses stage (zg - z0) % NST, in the phase ((zg - z0) / NST) & 1 of its barrier
+    auto tstage = [&](int zg) { return (zg - z0) % NST; };
+    auto tphase = [&](int zg) { return (unsigned)((zg - z0) / NST) & 1u; };
     V4<R>* sing = reinterpret_cast<V4<R>*>(rest);                    // [NING][P1]
     R* sphi = reinterpret_cast<R*>(sing + G::NING * G::P1);          // [NPHI][P2]
     R* cst = sphi + G::NPHI * G::P2;                                 // [2][P1] c^n on the ring
@@ -917,7 +927,7 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
     auto tma_issue = [&](int zg) {
         if constexpr (TMA) {
             if (threadIdx.y == 0) {
-                const int sidx = (zg - z0) & 1;
+                const int sidx = tstage(zg);
                 if (tl == 0) mbar_arrive_expect_tx(&bars[sidx], (unsigned)(TSTAGE * sizeof(R)));
                 __syncwarp();
                 if (tl < Q0) {
@@ -931,12 +941,11 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
     bool tma_late = false;           // a wait ran out (reported through err)
     if constexpr (TMA) {
         if (G::tid() == 0) {
-            mbar_init(&bars[0], 1);
-            mbar_init(&bars[1], 1);
+            for (int i = 0; i < NST; ++i) mbar_init(&bars[i], 1);
             fence_proxy_async();
         }
         __syncwarp();                // the first warp issues right after the initialisation
-        tma_issue(z0);
+        for (int d = 0; d < NST - 1 && z0 + d < z1; ++d) tma_issue(z0 + d);
     }
 
     for (int zg = z0 - 2; zg <= z0 + 1; ++zg) async_phi_plane<L, G>(P, phi_n, fslot(zg), zg, halo);
@@ -961,18 +970,19 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
             // prefetch for the next plane: phi plane z+3 into the slot of z-2, ring of z+2
             async_phi_plane<L, G>(P, phi_n, fslot(z + 3), z + 3, halo);
             fetch_ring(z + 2);
-            tma_issue(z + 1);        // its stage was last read by pull(z-1), done everywhere
         }
+        // NST - 1 planes ahead; the stage was last read by pull(z-1), done everywhere
+        if (z + NST - 1 < z1) tma_issue(z + NST - 1);
         cp_async_commit();
         if (active_xy)
             pull_load<LP, SP, IS_PHI, WALLS, I, TMA>(K, fin, c_n, x, y, z, inside1 && z >= 1 && z + 1 < P.nz, st);
         ingredients(islot(z + 1), fslot(z), fslot(z + 1), fslot(z + 2), z + 1);
         __syncthreads();
         if constexpr (TMA) {
-            const int sidx = (z - z0) & 1;
+            const int sidx = tstage(z);
             // after one wait has run out the block stops waiting (its results are
             // flagged through err), so a broken copy costs about a second, not one per plane
-            if (!tma_late && !mbar_wait(&bars[sidx], (unsigned)((z - z0) >> 1) & 1u)) tma_late = true;
+            if (!tma_late && !mbar_wait(&bars[sidx], tphase(z))) tma_late = true;
             const bool edge = active_xy && (y == 0 || y == P.ny - 1);
             const bool fix = __any_sync(0xffffffffu, edge);
             if (active_xy)
@@ -990,7 +1000,7 @@ __device__ __forceinline__ void march(const KParams& K, const typename SP::store
             // report, and give a copy still in flight a last bounded wait
             // before the block's shared memory is released
             atomicExch(err, 1);
-            mbar_wait(&bars[(z1 - 1 - z0) & 1], (unsigned)((z1 - 1 - z0) >> 1) & 1u);
+            mbar_wait(&bars[tstage(z1 - 1)], tphase(z1 - 1));
         }
     }
 }
@@ -1001,7 +1011,9 @@ constexpr size_t march_smem(bool is_phi, bool tma = false) {
     using R = typename SP::real;
     return sizeof(V4<R>) * G::NING * G::P1 + sizeof(R) * G::NPHI * G::P2 + sizeof(R) * 2 * G::P1 +
            (is_phi ? sizeof(R) * G::NING * G::P1 : sizeof(R) * 2 * G::P1) +
-           (tma ? 2 * sizeof(R) * (is_phi ? ex0_count<L>() : ex0_count<LH>()) * BX * BY + 16 : 0);
+           (tma ? (LBPF_TMA_STAGES * (sizeof(R) * (is_phi ? ex0_count<L>() : ex0_count<LH>()) * BX * BY + 8) + 127) /
+                      128 * 128
+                : 0);
 }
 
 // ---- the two step kernels ----------------------------------------------------------
