@@ -186,6 +186,8 @@ bool encode_pop_map(CUtensorMap* m, void* base, const StepParams& P, int q, int 
 int pick_zch(long long tiles, int nz, long long resident, int def) {
     auto waves = [&](int z) { return (double)(tiles * ((nz + z - 1) / z)) / (double)resident; };
     if (waves(def) >= 3.0) return def;
+    for (int z : {24, 16, 12, 8})
+        if (waves(z) >= 3.0) return z;
     int best = def;
     double best_fill = -1.0;
     for (int z : {8, 12, 16, 24}) {
@@ -234,11 +236,12 @@ struct Impl {
         ctx->zch_c = ZCHC;
         if constexpr (L::D == 3) {
             // 3-D: planes per block.  Grids of at least 3 waves of resident blocks
-            // at the default chunk keep it; smaller ones take the chunk of 8, 12,
-            // 16 or 24 planes whose last wave is fullest among those with at
-            // least 1.5 waves (the longer on a tie): on GB300 128^3 went from
-            // 12.2 to 13.5 GLUPS (12 planes), 160^3 from 12.8 to 14.2 (8),
-            // 192^3 from 15.0 to 15.3 (16); 256^3 keeps 32.
+            // at the default chunk keep it; smaller ones take the longest chunk of
+            // 24, 16, 12 or 8 planes that still gives 3 waves, else the one whose
+            // last wave is fullest among those with at least 1.5 waves (the
+            // longer on a tie): on GB300 128^3 went from 12.2 to 13.5 GLUPS (12
+            // planes), 160^3 from 12.8 to 14.6 (12), 192^3 from 15.0 to 15.3
+            // (16); 256^3 keeps 32.
             int sms = 0, occ_phi = 0, occ_c = 0;
             const bool w = walls(ctx);
             LBPF_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
