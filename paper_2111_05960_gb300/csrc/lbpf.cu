@@ -83,14 +83,15 @@ namespace {
 #ifndef LBPF_MINB2_F64
 #define LBPF_MINB2_F64 6
 #endif
-// 3-D, FP32 arithmetic (FP32 and 16-bit storage): 32 x 4 tiles, 32 planes,
-// 6 blocks per SM; FP64: 32 x 8 tiles, 16 planes, 2 blocks per SM (register
-// bound).  Chosen by timing the 256^3 porous step on GB300.
+// 3-D, FP32 arithmetic (FP32 and 16-bit storage): 32 x 4 tiles, 48 planes
+// (at 256^3: 6 chunks, the last of 16 planes, 3.4 waves of blocks), 6 blocks
+// per SM; FP64: 32 x 8 tiles, 16 planes, 2 blocks per SM (register bound).
+// Chosen by timing the 256^3 porous step on GB300.
 #ifndef LBPF_BY3
 #define LBPF_BY3 4
 #endif
 #ifndef LBPF_ZCH3
-#define LBPF_ZCH3 32
+#define LBPF_ZCH3 48
 #endif
 #ifndef LBPF_MINB3
 #define LBPF_MINB3 6
