@@ -107,15 +107,15 @@ namespace {
 #endif
 // The composition kernel with h on D3Q7 pulls 7 instead of 19 populations, so
 // its ingredient work (the D3Q19 gradient on the tile's ring) weighs more and
-// it gets its own FP32 tile: 32 x 8 with 16 planes and 4 blocks per SM
+// it gets its own FP32 tile: 32 x 8 with 24 planes and 4 blocks per SM
 // (64 registers, no spills) recomputes a smaller share of ring nodes than
 // 32 x 4 and ran 2.5% faster on the 256^3 step (16 x 32 and 6 blocks of 32 x 4
-// were slower).
+// were slower); 24 planes per block ran 1.6% faster than 16, 32 or 48.
 #ifndef LBPF_BY3_HS
 #define LBPF_BY3_HS 8
 #endif
 #ifndef LBPF_ZCH3_HS
-#define LBPF_ZCH3_HS 16
+#define LBPF_ZCH3_HS 24
 #endif
 #ifndef LBPF_MINB3_HS
 #define LBPF_MINB3_HS 4
