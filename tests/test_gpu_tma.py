@@ -1,8 +1,9 @@
 """The step kernels' opt-in tensor-map pulls (LBPF_TMA=1; FP32 storage, D3Q19,
 periodic domains): the copy engine brings each plane's rows of the links with
 e_x = 0 into shared memory (the other links are loaded by the threads), and
-the threads on the grid's y faces reload the rows that wrap.  The arithmetic is that of the load path, so both must give the
-same bits; one case is also held against the FP64 oracle."""
+the threads on the grid's y faces reload the rows that wrap.  The arithmetic
+is that of the load path, so both must give the same bits; one case is also
+held against the FP64 oracle."""
 import os
 
 import numpy as np
