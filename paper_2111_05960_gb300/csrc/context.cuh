@@ -83,6 +83,7 @@ struct lbpf_ctx {
     int corr_blocks = 0;
     long long corr_stride = 1;
     int mass_blocks = 0;
+    int sm_count = 0;              // multiprocessors of the context's device
     int zch_phi = 0, zch_c = 0;    // planes per block of the z-marching step kernels
     int cur = 0;
     int64_t step = 0;

@@ -753,6 +753,7 @@ lbpf_status lbpf_create(const lbpf_params* p, const double* phi0, const double* 
     }
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    ctx->sm_count = sms;
     const long long want = (ctx->sp.N + kMassThreads - 1) / kMassThreads;
     ctx->mass_blocks = (int)std::min<long long>(want, 4LL * sms);
     if (ctx->mass_blocks < 1) ctx->mass_blocks = 1;
