@@ -383,7 +383,7 @@ struct Impl {
     }
     // mass correction after a composition step whose new state has parity `cur_after`
     static void launch_corr_p(lbpf_ctx* ctx, MassCorr* mc, void* c, void* h) {
-        k_mass_corr_plan<<<1, kMassThreads, 0, ctx->stream>>>(ctx->corr_partials, ctx->corr_blocks, mc,
+        k_mass_corr_plan<<<1, kPlanThreads, 0, ctx->stream>>>(ctx->corr_partials, ctx->corr_blocks, mc,
                                                              ctx->sp.N, kCorrDelta);
         k_mass_corr_apply<SP><<<64, 256, 0, ctx->stream>>>(mc, (R*)c, (S*)h, ctx->sp.N, ctx->corr_stride);
     }

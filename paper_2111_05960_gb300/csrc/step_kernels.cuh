@@ -1225,6 +1225,7 @@ k_mass_partial(const R* __restrict__ c, const R* __restrict__ phi, long long n, 
         const float4* c4 = reinterpret_cast<const float4*>(c);
         const float4* p4 = reinterpret_cast<const float4*>(phi);
         unsigned nbad = 0;
+        float lc = 0.0f, lp = 0.0f;
         auto take = [&](float cv, float pv, MassAcc<float>& ac, MassAcc<float>& ap) {
             ac.add(cv, 0.0f);
             ap.add(pv, 0.0f);
@@ -1247,8 +1248,12 @@ k_mass_partial(const R* __restrict__ c, const R* __restrict__ phi, long long n, 
                 take(cv[u].z, pv[u].z, ac, ap);
                 take(cv[u].w, pv[u].w, ac, ap);
             }
-            sc += (double)ac.hi + (double)ac.lo;
-            sp += (double)ap.hi + (double)ap.lo;
+            // the small parts go on in FP32 (each is a few ulps of its round's
+            // sum): one conversion and one FP64 add per field and round
+            sc += (double)ac.hi;
+            sp += (double)ap.hi;
+            lc += ac.lo;
+            lp += ap.lo;
         }
         if (blockIdx.x == 0) {               // the last n mod 4 values
             for (long long i = 4 * n4 + threadIdx.x; i < n; i += kMassThreads) {
@@ -1258,6 +1263,8 @@ k_mass_partial(const R* __restrict__ c, const R* __restrict__ phi, long long n, 
                 sp += (double)ap.hi;
             }
         }
+        sc += (double)lc;
+        sp += (double)lp;
         bad = (double)nbad;
     } else {
         const long long n2 = n / 2;
@@ -1330,15 +1337,25 @@ struct MassCorr {
     unsigned long long round;  // corrections planned so far (rotates the node subset)
 };
 
-static __global__ void __launch_bounds__(kMassThreads)
+// One block of kPlanThreads: the partial sums (one per composition-kernel
+// block, thousands) take a few loads per thread.
+constexpr int kPlanThreads = 1024;
+static __global__ void __launch_bounds__(kPlanThreads)
 k_mass_corr_plan(const double* __restrict__ partials, int nblocks, MassCorr* __restrict__ mc, long long N,
                  double delta_target) {
-    double sc = 0.0, d1 = 0.0, d2 = 0.0;
+    __shared__ double red[kPlanThreads / 32];
+    double sc = 0.0;
     // unrolled so that a thread's loads are in flight together (the adds keep
     // their order, so the sum does not depend on the unrolling)
-#pragma unroll 16
-    for (int b = threadIdx.x; b < nblocks; b += kMassThreads) sc += partials[b];
-    block_sum3<double>(sc, d1, d2);
+#pragma unroll 4
+    for (int b = threadIdx.x; b < nblocks; b += kPlanThreads) sc += partials[b];
+    for (int o = 16; o > 0; o >>= 1) sc += __shfl_down_sync(0xffffffffu, sc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        sc = red[threadIdx.x];
+        for (int o = 16; o > 0; o >>= 1) sc += __shfl_down_sync(0xffffffffu, sc, o);
+    }
     if (threadIdx.x == 0) {
         const double dM = mc->target - sc;
         long long k = 0;
